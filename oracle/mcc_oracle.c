@@ -222,8 +222,10 @@ int orc_pairs(const int64_t* offsets, int32_t n_cells, int32_t n_species, int32_
 
 /* ------------------------------------------------------------------------------------------------------------
  * N97 angle parameter A(s): the root of L(A) = coth(A) - 1/A = exp(-s) (the mean of cos(chi) for the
- * distribution proportional to exp(A cos chi) equals exp(-s)). L is evaluated from the Laurent series of coth
- * (Bernoulli numbers) below A = 1/2 and directly above; the root is found by bisection to the last bit.
+ * distribution proportional to exp(A cos chi) equals exp(-s)). Solved in the equivalent form
+ * G(A) = 1 - L(A) = -expm1(-s), which keeps full relative precision when s is small and A large. L is evaluated
+ * from the Laurent series of coth (Bernoulli numbers) below A = 1/2; above it G = 1/A - 2/expm1(2A). The root is
+ * found by bisection to the last bit.
  * ---------------------------------------------------------------------------------------------------------- */
 double orc_n97_L(double A)
 {
@@ -244,27 +246,34 @@ double orc_n97_L(double A)
     return 1.0 / tanh(A) - 1.0 / A;
 }
 
+/* G(A) = 1 - L(A); coth(A) - 1 = 2 / expm1(2A) */
+static double n97_G(double A)
+{
+    if (A < 0.5) return 1.0 - orc_n97_L(A);
+    return 1.0 / A - 2.0 / expm1(2.0 * A);
+}
+
 double orc_n97_A(double s)
 {
-    double y = exp(-s);
-    if (!(y > 0.0)) return 0.0;   /* s so large that exp(-s) underflows: isotropic limit A -> 0 */
-    if (!(y < 1.0)) return INFINITY; /* s == 0: no scattering */
-    /* L(A) > 1 - 1/A, so L(hi) > y for hi = 1/(1-y) + 1. */
-    double lo = 0.0, hi = 1.0 / (-expm1(-s)) + 1.0;
+    double z = -expm1(-s); /* 1 - exp(-s) */
+    if (!(z < 1.0)) return 0.0;       /* exp(-s) underflows: isotropic limit A -> 0 */
+    if (!(z > 0.0)) return INFINITY;  /* s == 0: no scattering */
+    /* G is decreasing from 1 to 0; G(A) < 1/A, so G(hi) < z for hi = 1/z + 1. */
+    double lo = 0.0, hi = 1.0 / z + 1.0;
     for (int it = 0; it < 4000; ++it) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (orc_n97_L(mid) < y) lo = mid; else hi = mid;
+        if (n97_G(mid) > z) lo = mid; else hi = mid;
     }
     /* the bracket has collapsed to adjacent doubles: return the one with the smaller residual */
-    return fabs(orc_n97_L(lo) - y) <= fabs(orc_n97_L(hi) - y) ? lo : hi;
+    return fabs(n97_G(lo) - z) <= fabs(n97_G(hi) - z) ? lo : hi;
 }
 
 /* Centre-of-mass polar angle from the scattering length s (returns sin(Theta) and 1 - cos(Theta)).
  *  TA77: tan(Theta/2) = delta ~ N(0, s/2) (variance fixed by s = <Theta^2>/2 of Eq. sij_sji), drawn by
  *        Box-Muller from U1 (radius) and U4 (angle); sin = 2 delta/(1+delta^2), 1-cos = 2 delta^2/(1+delta^2).
  *  N97:  cos chi drawn from the density proportional to exp(A cos chi) by inverting its CDF with V = U1:
- *        1 - cos chi = -log1p(V expm1(-2A)) / A. */
+ *        1 - cos chi = -log1p(V expm1(-2A)) / A, and 1 + cos chi = log1p((1 - V) expm1(2A)) / A for sin chi. */
 void orc_angle(int32_t method, double s, double U1, double U4, double* sin_theta, double* one_minus_cos)
 {
     if (method == ORC_TA77) {
@@ -283,14 +292,24 @@ void orc_angle(int32_t method, double s, double U1, double U4, double* sin_theta
         return;
     }
     double A = orc_n97_A(s);
-    double omc;
-    if (A == 0.0) omc = 2.0 * U1;
-    else if (isinf(A)) omc = 0.0;
-    else omc = -log1p(U1 * expm1(-2.0 * A)) / A;
+    double omc, opc;
+    if (A == 0.0) { omc = 2.0 * U1; opc = 2.0 * (1.0 - U1); }
+    else if (isinf(A)) { omc = 0.0; opc = 2.0; }
+    else {
+        /* 1 - cos chi = -ln(1 + x) / A with 1 + x = (1 - V) + V exp(-2A), x = -V (1 - exp(-2A)): log1p(x) while x is
+         * small, the sum of the two positive terms once it is not (no cancellation either way) */
+        double x = -U1 * -expm1(-2.0 * A);
+        omc = x > -0.5 ? -log1p(x) / A : -log((1.0 - U1) + U1 * exp(-2.0 * A)) / A;
+        /* 1 + cos chi = log1p((1 - V) expm1(2A)) / A from the same inversion, so sin chi stays accurate near
+         * back-scatter where 2 - (1 - cos chi) would cancel */
+        opc = omc <= 1.0 ? 2.0 - omc : log1p((1.0 - U1) * expm1(2.0 * A)) / A;
+    }
     if (omc < 0.0) omc = 0.0;
     if (omc > 2.0) omc = 2.0;
+    if (opc < 0.0) opc = 0.0;
+    if (opc > 2.0) opc = 2.0;
     *one_minus_cos = omc;
-    *sin_theta = sqrt(omc * (2.0 - omc));
+    *sin_theta = sqrt(omc * opc);
 }
 
 /* Rotation of the relative velocity u through polar angle Theta and azimuth phi about its own direction
@@ -339,9 +358,15 @@ static void rel_cm(double c, double ma, double mb, const double ui[3], const dou
     double Minv = sqrt((ma + mb) * (ma + mb) + 2.0 * ma * mb * grm1);
     *gC = M / Minv;
     double coef_b = (*gC) * (*gC) / (c2 * ((*gC) + 1.0)); /* (gamma_C - 1)/|V|^2 */
-    double Vp = V[0] * ma * ui[0] + V[1] * ma * ui[1] + V[2] * ma * ui[2];
-    double f = coef_b * Vp - (*gC) * ma * gi;
-    for (int d = 0; d < 3; ++d) pstar[d] = ma * ui[d] + f * V[d];
+    /* p* = q + (gamma_C - 1)(Vhat.q) Vhat with q = (E_j p_i - E_i p_j) / E_tot: the boost of p_i to the CM frame
+     * written through the pair's difference, m_a m_b (gamma_j (u_i - u_j) - (gamma_i - gamma_j) u_j) / M, so that
+     * co-moving pairs do not cancel */
+    double q[3], Vq = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        q[d] = ma * mb * (gj * (ui[d] - uj[d]) - dg * uj[d]) / M;
+        Vq += V[d] * q[d];
+    }
+    for (int d = 0; d < 3; ++d) pstar[d] = q[d] + coef_b * Vq * V[d];
     double p2 = pstar[0] * pstar[0] + pstar[1] * pstar[1] + pstar[2] * pstar[2];
     *pmag = sqrt(p2);
     double gsa = sqrt(1.0 + p2 / (ma * ma * c2)), gsb = sqrt(1.0 + p2 / (mb * mb * c2));
@@ -552,15 +577,15 @@ void orc_energy_pair(int32_t relativistic, double c, double m1, double m2, doubl
 /* ------------------------------------------------------------------------------------------------------------
  * Moment correction of one interaction in one cell [Algorithm 1 after the pair loop; Sec. 4; Appendix A].
  * ---------------------------------------------------------------------------------------------------------- */
-typedef struct { uint64_t key; double w; int32_t idx; } sort_item;
-
-static int cmp_weight_desc(const void* a, const void* b)
+/* Sort key of the optional weight-descending order: the weight's IEEE bits (weights are positive, so the bits
+ * order like the values) inverted for descending order, truncated to sign, exponent and 32 mantissa bits, with the
+ * particle's rank in the random permutation in the low 20 bits. Weights that agree to 2^-32 relative therefore tie
+ * and keep the random order. */
+static uint64_t weight_key(double w, uint32_t rank)
 {
-    const sort_item* x = (const sort_item*)a;
-    const sort_item* y = (const sort_item*)b;
-    if (x->w > y->w) return -1;
-    if (x->w < y->w) return 1;
-    return (x->key > y->key) - (x->key < y->key);
+    uint64_t b;
+    memcpy(&b, &w, sizeof b);
+    return (~b & ~(uint64_t)(PERM_MAX_N - 1)) | (uint64_t)rank;
 }
 
 /* Kinetic energy of one particle of mass mp (weighted) with state v (velocity or proper velocity). */
@@ -674,6 +699,11 @@ static void correct_cell(const state_t* st, int32_t c, const double* m, int32_t 
         else if (dE != 0.0) fail = 1;
     }
 
+    /* "Delta E_s = 0" (Algorithm 1, loop exit) is read as: no larger than 64 ulps of species s's post-shift kinetic
+     * energy. Below that the violation is rounding noise of the sums (it is what equal weights leave). */
+    for (int side = 0; side < 2; ++side)
+        if (fabs(D[side]) <= 0x1p-47 * Es[side]) D[side] = 0.0;
+
     /* energy-correction loops, species a then b */
     for (int side = 0; side < nside && !fail; ++side) {
         if (D[side] == 0.0) continue;
@@ -683,15 +713,11 @@ static void correct_cell(const state_t* st, int32_t c, const double* m, int32_t 
         orc_permutation(n, p->seed, p->step, (uint32_t)c, (uint32_t)inter, (uint32_t)side, perm);
         if (p->sort_by_weight) {
             /* optional step of Algorithm 1: descending weight; ties keep the random order */
-            sort_item* items = (sort_item*)malloc(sizeof(sort_item) * (size_t)n);
-            for (int64_t r = 0; r < n; ++r) {
-                items[r].idx = perm[r];
-                items[r].w = st->w[s0[side] + perm[r]];
-                items[r].key = (uint64_t)r;
-            }
-            qsort(items, (size_t)n, sizeof(sort_item), cmp_weight_desc);
-            for (int64_t r = 0; r < n; ++r) rho[r] = s0[side] + items[r].idx;
-            free(items);
+            uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+            for (int64_t r = 0; r < n; ++r) keys[r] = weight_key(st->w[s0[side] + perm[r]], (uint32_t)r);
+            qsort(keys, (size_t)n, sizeof(uint64_t), cmp_u64);
+            for (int64_t r = 0; r < n; ++r) rho[r] = s0[side] + perm[keys[r] & (PERM_MAX_N - 1)];
+            free(keys);
         } else {
             for (int64_t r = 0; r < n; ++r) rho[r] = s0[side] + perm[r];
         }

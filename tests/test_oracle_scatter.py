@@ -28,10 +28,11 @@ def A_ref(s):
         return float(mpmath.findroot(f, (lo, hi), solver="anderson"))
 
 
-@pytest.mark.parametrize("s", [1e-4, 1e-2, 0.1, 0.5, 1.0, 3.0, 6.0])
+@pytest.mark.parametrize("s", [1e-9, 1e-7, 1e-4, 1e-2, 0.1, 0.5, 1.0, 3.0, 6.0])
 def test_n97_root_matches_independent_solve(s):
+    # full relative precision also for tiny s (A ~ 1/s), where solving with exp(-s) would lose digits
     A = O.n97_A(s)
-    assert A == pytest.approx(A_ref(s), rel=1e-11)
+    assert A == pytest.approx(A_ref(s), rel=1e-13)
 
 
 def test_n97_limits():
@@ -68,6 +69,25 @@ def test_n97_mean_cos_is_exp_minus_s(s):
         assert O.angle(O.N97, s, v, 0.5)[1] == pytest.approx(f(v), rel=1e-10, abs=1e-15)
     st, omc1 = O.angle(O.N97, s, 0.3, 0.5)
     assert st ** 2 == pytest.approx(omc1 * (2 - omc1), rel=1e-12)
+    # sin chi near back-scatter equals the 40-digit value of sqrt((1 - cos)(1 + cos)) from the inverse CDF
+    with mpmath.workdps(40):
+        Am = mpmath.mpf(A)
+        for v in [0.999, 0.9999999]:
+            cosx = 1 + mpmath.log(mpmath.mpf(1 - v) + mpmath.mpf(v) * mpmath.exp(-2 * Am)) / Am
+            ref = float(mpmath.sqrt((1 - cosx) * (1 + cosx)))
+            assert O.angle(O.N97, s, v, 0.5)[0] == pytest.approx(ref, rel=1e-9, abs=1e-300)
+
+
+@pytest.mark.parametrize("s", [1e-3, 0.05, 0.3])
+def test_n97_cos_accurate_when_A_times_angle_is_large(s):
+    """Large A with V near 1 puts 1 + V expm1(-2A) close to zero; 1 - cos chi must still be accurate (40-digit
+    reference of -ln(1 - V + V exp(-2A)) / A)."""
+    A = O.n97_A(s)
+    with mpmath.workdps(40):
+        Am = mpmath.mpf(A)
+        for v in [0.9, 0.999, 1 - 2.0 ** -23]:
+            ref = float(-mpmath.log(1 - mpmath.mpf(v) + mpmath.mpf(v) * mpmath.exp(-2 * Am)) / Am)
+            assert O.angle(O.N97, s, v, 0.5)[1] == pytest.approx(ref, rel=1e-12)
 
 
 @pytest.mark.parametrize("s", [1e-3, 0.05, 0.8])
