@@ -1,0 +1,324 @@
+"""Benchmark of the fused collision step on the three-species plasma (2^18 cells, log-normal counts with mean 512,
+about 1.34e8 particles, N97, float velocities with double weights and float-float moment sums).
+
+One step = one pass of the whole collision step over every cell and interaction (pairing, scatter, momentum and
+energy correction), one persistent kernel launch. K steps are captured in one CUDA graph and timed with CUDA events
+on the launching stream; the state (4.3 GB read + written per step) is far larger than L2, so no flush is needed.
+
+Prints one JSON line: collision pairs/s (scatter pairs of all interactions; a triplet counts three) with the HBM
+roofline of the step kernel, the end-to-end figure through host buffers, the plain FP64 GPU step on the same
+workload, and the oracle timed on the host cores on a bounded sample of cells.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collision pairs/sec"
+UNIT = "pairs/s"
+BYTES_PER_PARTICLE = {"f32": 32, "f64": 56}  # read v (12|24) + w (8), write v (12|24)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=1 << 18, help="cells of the three-species workload")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mcc_cell.cu", "mcc_device.cuh", "mcc_kernels.h"):
+        with open(os.path.join(ROOT, "paper_2407_19151_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken on this kernel
+    source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("kernel_source") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            sm = [float(r[0]) for r in rows]
+            mx = [float(r[1]) for r in rows]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].strip().lower() == "active"})
+            return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": reasons,
+                    "samples": len(rows)}
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def make_workload(cells: int, rank: int, precision: str):
+    from paper_2407_19151_gb300 import workloads as W
+    return W.three_species(n_cells=cells, data_seed=1239 + 1000 * rank, precision=precision)
+
+
+def cpu_baseline(wl, budget_s: float = 15.0):
+    """The oracle as it stands on the host cores (OpenMP over cells), on the first cells of the same workload:
+    grows the sample until a run takes a few seconds, then reports pairs/s."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    k = 64
+    spent = 0.0
+    best = None
+    while True:
+        sub = wl.subset(k)
+        st = O.State(sub.vx.astype(np.float64), sub.vy.astype(np.float64), sub.vz.astype(np.float64), sub.w,
+                     sub.offsets, sub.n_cells, sub.n_species)
+        p = O.Params(method=sub.method, dt=sub.dt, dV=sub.dV, eps0=sub.eps0, c=sub.c, fE=sub.fE, seed=sub.seed)
+        t0 = time.perf_counter()
+        O.step(st, sub.q, sub.m, sub.lnL, p, n_steps=1)
+        dt = time.perf_counter() - t0
+        spent += dt
+        best = (sub.pairs_per_step() / dt, k, dt)
+        if dt > budget_s / 3 or spent > budget_s or k >= wl.n_cells:
+            break
+        k = min(wl.n_cells, int(k * max(2.0, (budget_s / 3) / max(dt, 1e-3))))
+    return {"value": best[0], "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+            "sample": f"one step of the first {best[1]} cells ({best[2]:.1f} s, FP64 C oracle, OpenMP over cells)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.cells, 0, "f32")
+    cb = cpu_baseline(wl, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "three_species", "n_cells": wl.n_cells, "n_particles": wl.n},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2407_19151_gb300 as mcc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mcc.build()
+    ctx = mcc.context(local)
+
+    wl = make_workload(args.cells, rank, "f32")
+    N, C, S = wl.n, wl.n_cells, wl.n_species
+    pairs = wl.pairs_per_step()
+    species = list(zip(wl.q.tolist(), wl.m.tolist()))
+    max_cell = int(wl.counts.sum(axis=1).max())
+    off = torch.from_numpy(wl.offsets).to(dev)
+    w = torch.from_numpy(wl.w).to(dev)
+    v = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (wl.vx, wl.vy, wl.vz)]
+    corr = torch.zeros(C, dtype=torch.int32, device=dev)
+    fail = torch.zeros(C, dtype=torch.int32, device=dev)
+    params = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
+
+    def step(k0, nsteps=1):
+        params.step = k0
+        mcc.mcc_step_fused(*v, w, off, C, S, species, wl.lnL, params, n_steps=nsteps, max_cell=max_cell,
+                           corr_pairs=corr, fail_count=fail)
+
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    mcc.sync_status(local)
+
+    # K steps captured in one CUDA graph (one memset + one persistent kernel per step)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step(args.warmup, args.steps)
+    launches_before = ctx.launch_count()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    mcc.sync_status(local)
+    ms_step = ms / args.steps
+    value = pairs * world / (ms_step * 1e-3)
+    hbm, peak_kind = peaks()
+    algo_bytes = BYTES_PER_PARTICLE["f32"] * N
+    achieved = algo_bytes / (ms_step * 1e-3) / 1e9
+    traffic = ncu_traffic("three_species")
+    fails = int(fail.sum().item())
+
+    # end to end through host buffers: H2D of the step's inputs, the step, D2H of the updated velocities
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (wl.vx, wl.vy, wl.vz)]
+        host_w = torch.from_numpy(wl.w).pin_memory()
+        out = [torch.empty_like(h).pin_memory() for h in host]
+        e2e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize(dev)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(e2e_steps):
+            for dst, src in zip(v, host):
+                dst.copy_(src, non_blocking=True)
+            w.copy_(host_w, non_blocking=True)
+            step(1000 + k)
+            for dst, src in zip(out, v):
+                dst.copy_(src, non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = t0.elapsed_time(t1) / e2e_steps
+        bi = sum(h.numel() * h.element_size() for h in host) + host_w.numel() * 8
+        bo = sum(h.numel() * h.element_size() for h in out)
+        e2e = {"value": pairs * world / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": e_ms}
+
+    # plain FP64 GPU step on the same workload (the comparison point of the mixed path)
+    fp64 = None
+    if args.fp64_steps > 0:
+        v64 = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev) for x in (wl.vx, wl.vy, wl.vz)]
+        p64 = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
+        mcc.mcc_step_fused(*v64, w, off, C, S, species, wl.lnL, p64, n_steps=1, max_cell=max_cell,
+                           corr_pairs=corr, fail_count=fail)
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        p64.step = 1
+        mcc.mcc_step_fused(*v64, w, off, C, S, species, wl.lnL, p64, n_steps=args.fp64_steps, max_cell=max_cell,
+                           corr_pairs=corr, fail_count=fail)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms = f0.elapsed_time(f1) / args.fp64_steps
+        fp64 = {"value": pairs * world / (f_ms * 1e-3), "unit": UNIT, "ms_per_step": f_ms,
+                "roofline_frac_hbm": BYTES_PER_PARTICLE["f64"] * N / (f_ms * 1e-3) / 1e9 / hbm,
+                "speedup_of_mixed": f_ms / ms_step}
+        del v64
+        mcc.sync_status(local)
+
+    if rank != 0:
+        return
+    cb = None if (args.no_cpu or world > 1) else cpu_baseline(wl)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "three_species", "n_cells": C, "n_particles": N, "species": S,
+                   "interactions": len(wl.interactions()), "pairs_per_step": pairs, "method": "N97",
+                   "precision": "f32 velocities and kinematics, f64 weights, float-float sums, f64 coefficients",
+                   "max_cell": max_cell, "graph_steps": args.steps,
+                   "l2": "no flush: 4.3 GB state per step, far larger than the 129 MB L2",
+                   "parallelism": f"cells, {world} independent shard(s)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes": f"{BYTES_PER_PARTICLE['f32']} B/particle x {N} particles per launch"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": args.steps,  # one persistent step kernel per captured step
+        "correction_failures": fails,
+        "fp64_step": fp64,
+        "cpu_baseline": cb,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

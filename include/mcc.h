@@ -1,0 +1,199 @@
+/*
+ * mcc.h: C ABI of the GB300 (sm_103a) Monte-Carlo Coulomb collision step for weighted particles with exact
+ * momentum and energy conservation (Angus et al., "Moment-preserving Monte-Carlo Coulomb collision method for
+ * particle codes").
+ *
+ * The calls follow the paper's statement of the problem: weighted macro-particles in cells of volume dV
+ * (Sec. 2, Eq. Klimintovich), a binary interaction between two species (Sec. 3, Sec. 4), and the steps of
+ * Algorithm 1.
+ *
+ * Conventions (every entry point):
+ *  - Device arrays are owned by the caller; the library never allocates per call. Host arrays are read before the
+ *    call returns.
+ *  - Every call is asynchronous on the stream it is given (0 = the legacy default stream) and returns MCC_OK once
+ *    its work is enqueued. Argument errors detectable on the host are returned immediately and nothing is enqueued.
+ *    Errors found on the device (a cell larger than the declared maximum, a failed energy correction under
+ *    MCC_FAIL_ERROR, an invalid segment) are latched in the context's device status word and returned by
+ *    mcc_sync_status.
+ *  - Particles are stored binned (see mcc_bin): all particles of cell c and species s are contiguous in
+ *    [offsets[c*S + s], offsets[c*S + s + 1]), cells in order, species in order within a cell.
+ *  - Velocities are structure-of-arrays vx, vy, vz of doubles (MCC_F64) or floats (MCC_F32_MIXED); weights are
+ *    always doubles and must be positive and finite. In relativistic mode the stored quantity is the proper
+ *    velocity u = gamma v (Appendix A).
+ *  - No call traps or spins without a bound; no exception crosses the ABI.
+ */
+#ifndef MCC_H
+#define MCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcc_ctx mcc_ctx;
+typedef struct CUstream_st* mcc_stream; /* a cudaStream_t */
+
+typedef enum {
+    MCC_OK = 0,
+    MCC_ERR_INVALID_ARG = -1,
+    MCC_ERR_CUDA = -2,
+    MCC_ERR_WORKSPACE = -3,
+    MCC_ERR_TIMEOUT = -4,
+    MCC_ERR_CORRECTION_FAILED = -5,
+    MCC_ERR_BOUNDS = -6,
+    MCC_ERR_TOO_LARGE = -7
+} mcc_status;
+
+typedef enum { MCC_TA77 = 0, MCC_N97 = 1 } mcc_method;
+typedef enum { MCC_F64 = 0, MCC_F32_MIXED = 1 } mcc_precision;
+typedef enum { MCC_FAIL_ROLLBACK = 0, MCC_FAIL_MOMENTUM_ONLY = 1, MCC_FAIL_ERROR = 2 } mcc_fail_policy;
+
+/* Maximum species per call and maximum particles per (cell, species) segment. */
+#define MCC_MAX_SPECIES 8
+#define MCC_MAX_SEGMENT (1 << 20)
+
+/* Charge and (unweighted) mass of one species. */
+typedef struct {
+    double q;
+    double m;
+} mcc_species;
+
+/* Binned particle arrays on the device (caller-owned). prec selects float or double for vx, vy, vz. */
+typedef struct {
+    void* vx;
+    void* vy;
+    void* vz;
+    const double* w;
+    int64_t n;
+    int32_t prec; /* mcc_precision */
+} mcc_particles;
+
+/* Step parameters. dt, dV, eps0 enter the scattering length of Eq. sab_TA77; c is used in relativistic mode;
+ * fE is the energy-correction factor of Eq. U_inelastic; sort_by_weight is the optional sort of Algorithm 1;
+ * max_corr_passes bounds the energy-pair passes; correct = 0 runs the scatter alone. seed keys the random stream;
+ * step is the time-step index that enters every random counter (taken modulo 2^32). */
+typedef struct {
+    int32_t method;       /* mcc_method */
+    int32_t relativistic; /* 0 or 1 */
+    double dt, dV, eps0, c, fE;
+    int32_t sort_by_weight;
+    int32_t max_corr_passes;
+    int32_t fail_policy; /* mcc_fail_policy */
+    int32_t correct;
+    uint64_t seed;
+    uint64_t step;
+} mcc_params;
+
+/* Create / destroy a context on `device`. The context owns only a small device buffer (status word, work-queue
+ * counter) allocated here, once. */
+int mcc_create(mcc_ctx** ctx, int device);
+void mcc_destroy(mcc_ctx* ctx);
+
+/* Bytes of device workspace mcc_bin needs for n particles and n_keys = n_cells * n_species segments. */
+int mcc_bin_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t* bytes);
+
+/*
+ * mcc_bin: cell sort (Sec. 2: particles are collided per cell of volume dV).
+ * Stable counting sort of particle indices by key = cell[i] * n_species + species[i].
+ *   cell, species   [n] device int32, cell in [0, n_cells), species in [0, n_species)
+ *   perm_out        [n] device int32: perm_out[k] = index of the k-th particle in binned order; stable, so equal
+ *                   keys keep increasing index
+ *   offsets_out     [n_cells * n_species + 1] device int64: segment starts, offsets_out[last] = n
+ *   ws, ws_bytes    device workspace of at least mcc_bin_workspace_size bytes
+ * Out-of-range keys latch MCC_ERR_BOUNDS (those particles are dropped from the output).
+ * A segment larger than MCC_MAX_SEGMENT latches MCC_ERR_TOO_LARGE.
+ */
+int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
+            int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws, size_t ws_bytes,
+            mcc_stream stream);
+
+/* Gather a double or float array through perm: out[k] = in[perm[k]] (elem_bytes 4 or 8). */
+int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream);
+
+/*
+ * mcc_pair: random binary pairs of Takizuka-Abe for interaction `inter` between species sa <= sb
+ * (Sec. 3.2, Fig. TApairing; Algorithm 1, second step).
+ *  intra (sa == sb, n particles): n < 2 none; n even (p0,p1),(p2,p3),...; n odd: (p0,p1),(p1,p2),(p2,p0) with
+ *    half the scattering length (flag bit 0) then (p3,p4),...
+ *  inter: N_max pairs; pair k = (k-th of the larger population, (k mod N_min)-th of the smaller), each population
+ *    in its own random order. p is the random permutation: local indices sorted by a 64-bit key made of 44
+ *    Philox-4x32-10 bits (counter = {i/2, cell, step, inter<<8 | 1 + side}, key = seed) and the index (20 bits).
+ * Output slots: cell c's pairs start at offsets[c * n_species] (its first particle); a cell never has more pairs
+ * than particles, so pair_i / pair_j / pair_flags of length n suffice. Entries beyond a cell's pair count are not
+ * written. pair_i holds species-sa particles, pair_j species-sb particles, both as global binned indices.
+ */
+int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_species, int32_t sa, int32_t sb,
+             int32_t inter, uint64_t seed, uint64_t step, int32_t* pair_i, int32_t* pair_j, uint8_t* pair_flags,
+             mcc_stream stream);
+
+/*
+ * mcc_scatter: the pair loop of Algorithm 1 for interaction (sa, sb).
+ * For each pair in list order: s = q_a^2 q_b^2 lnL_ab w_max N_min dt / (4 pi eps0^2 mu^2 u^3 dV) (Eq. sab_TA77;
+ * N_min = N - 1 intra, halved for triplet pairs), TA77 or N97 angle, rotation of u about itself, the lighter particle
+ * updated, the heavier with probability w_min / w_max (Sec. 3.2). Pairs sharing a particle run in list order.
+ * Relativistic mode rotates the centre-of-momentum momentum instead.
+ *   sp[n_species], lnL[n_species * n_species]: host arrays (species constants, Coulomb logarithm per pair)
+ *   pair_*: output of mcc_pair for the same (sa, sb, inter, seed, step)
+ *   backup: device, 3 * n values of the particle precision ([x | y | z] planes, binned index): receives the
+ *           pre-scatter velocities of every particle of species sa and sb (used by mcc_correct)
+ */
+int mcc_scatter(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* offsets, int32_t n_cells,
+                int32_t n_species, const mcc_species* sp, const double* lnL, int32_t sa, int32_t sb, int32_t inter,
+                const int32_t* pair_i, const int32_t* pair_j, const uint8_t* pair_flags, const mcc_params* params,
+                void* backup, mcc_stream stream);
+
+/*
+ * mcc_correct: the moment correction of Algorithm 1 for interaction (sa, sb) (Sec. 4; Appendix A).
+ * Momentum shift v -= B w_p with B = sum m_p (v_ps - v_bs) / sum m_p w_p (Eq. vp_pm); energy violation (Eq. Econs)
+ * split between species (Eq. DeltaEs); per species, particles in descending weight order (ties in random order;
+ * optional) paired (r0,r1),(r2,r3),... then offset by one on the next pass, each pair's centre-of-mass energy lowered
+ * by U = sign(D) min(|D|, fE KE_cm) (Eqs. vp1_inelastic, vp2_inelastic, vrel_inelastic, U_inelastic) until D = 0.
+ * If D != 0 after max_corr_passes passes the fail policy applies (Sec. 5.2).
+ *   backup            the pre-scatter velocities written by mcc_scatter
+ *   corr_pairs_out    [n_cells] device int32 or NULL: energy pairs used per cell (written)
+ *   fail_flags_out    [n_cells] device int32 or NULL: 1 where the correction failed (written)
+ */
+int mcc_correct(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* offsets, int32_t n_cells,
+                int32_t n_species, const mcc_species* sp, int32_t sa, int32_t sb, int32_t inter,
+                const mcc_params* params, const void* backup, int32_t* corr_pairs_out, int32_t* fail_flags_out,
+                mcc_stream stream);
+
+/* Bytes of device workspace mcc_step_fused needs when some cells exceed the shared-memory tile (max_cell
+ * particles in the largest cell). Zero when every cell fits on chip. */
+int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t max_cell, size_t* bytes);
+
+/*
+ * mcc_step_fused: n_steps whole collision steps (Algorithm 1 for every interaction in list order, each step with
+ * index params->step + t) in one persistent kernel launch per step. Each CTA takes cells from a work queue, stages
+ * the cell in shared memory (or in its workspace slab when the cell is larger than the on-chip tile), runs pairing,
+ * scatter and correction for every interaction, and writes the cell back. The result equals the sequence
+ * mcc_pair / mcc_scatter / mcc_correct over the interactions.
+ *   interactions   host int32 [2 * n_inter], pairs (a, b) with a <= b; interaction k uses index k in the counters
+ *   max_cell       an upper bound on particles per cell (cells above it latch MCC_ERR_BOUNDS and are skipped)
+ *   corr_pairs     [n_cells] device int32 or NULL: accumulated energy pairs
+ *   fail_count     [n_cells] device int32 or NULL: accumulated failed corrections
+ *   ws, ws_bytes   workspace of mcc_step_workspace_size bytes (may be NULL / 0 when that size is 0)
+ */
+int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* offsets, int32_t n_cells,
+                   int32_t n_species, const mcc_species* sp, const double* lnL, const int32_t* interactions,
+                   int32_t n_inter, const mcc_params* params, int32_t n_steps, int32_t max_cell,
+                   int32_t* corr_pairs, int32_t* fail_count, void* ws, size_t ws_bytes, mcc_stream stream);
+
+/* Particles staged on chip per cell by mcc_step_fused (0 = automatic: min(largest cell, 2048, what fits in
+ * shared memory)). Cells above it run from the workspace slabs. Used by the autotuner. */
+int mcc_set_tile_cap(mcc_ctx* ctx, int32_t cap);
+
+/* Synchronise `stream`, read and clear the device status word; returns MCC_OK or the first latched error. */
+int mcc_sync_status(mcc_ctx* ctx, mcc_stream stream);
+
+/* Number of kernel launches enqueued through this context since creation (for launch accounting). */
+int64_t mcc_launch_count(mcc_ctx* ctx);
+
+const char* mcc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

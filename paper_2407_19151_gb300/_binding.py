@@ -1,0 +1,303 @@
+"""Thin ctypes binding of the C ABI in ``include/mcc.h``: argument marshalling between torch CUDA tensors and the
+library. Every step of the collision method runs in the CUDA library; nothing here computes on particles. If the
+library is not built the calls raise (there is no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+TA77, N97 = 0, 1
+F64, F32_MIXED = 0, 1
+FAIL_ROLLBACK, FAIL_MOMENTUM_ONLY, FAIL_ERROR = 0, 1, 2
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace missing or too small",
+          -4: "bounded wait timed out", -5: "energy correction could not absorb the violation",
+          -6: "index or cell size out of bounds", -7: "segment larger than supported"}
+
+
+class MccError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, 'unknown')} ({code})")
+        self.code = code
+
+
+class _Species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double)]
+
+
+class _Particles(C.Structure):
+    _fields_ = [("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("w", C.c_void_p),
+                ("n", C.c_int64), ("prec", C.c_int32)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("method", C.c_int32), ("relativistic", C.c_int32), ("dt", C.c_double), ("dV", C.c_double),
+                ("eps0", C.c_double), ("c", C.c_double), ("fE", C.c_double), ("sort_by_weight", C.c_int32),
+                ("max_corr_passes", C.c_int32), ("fail_policy", C.c_int32), ("correct", C.c_int32),
+                ("seed", C.c_uint64), ("step", C.c_uint64)]
+
+
+@dataclass
+class Params:
+    """Mirror of ``mcc_params``."""
+    method: int = N97
+    relativistic: bool = False
+    dt: float = 1.0
+    dV: float = 1.0
+    eps0: float = 1.0
+    c: float = 1.0
+    fE: float = 0.05
+    sort_by_weight: bool = True
+    max_corr_passes: int = 8
+    fail_policy: int = FAIL_ROLLBACK
+    correct: bool = True
+    seed: int = 0
+    step: int = 0
+
+    def _c(self) -> _Params:
+        return _Params(int(self.method), int(bool(self.relativistic)), float(self.dt), float(self.dV),
+                       float(self.eps0), float(self.c), float(self.fE), int(bool(self.sort_by_weight)),
+                       int(self.max_corr_passes), int(self.fail_policy), int(bool(self.correct)),
+                       int(self.seed) & (2**64 - 1), int(self.step) & (2**64 - 1))
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path}); run paper_2407_19151_gb300.build()")
+    L = C.CDLL(path)
+    P, vp = C.POINTER, C.c_void_p
+    sig = {
+        "mcc_create": (C.c_int, [P(vp), C.c_int]),
+        "mcc_destroy": (None, [vp]),
+        "mcc_bin_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
+        "mcc_bin": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
+        "mcc_gather": (C.c_int, [vp, vp, C.c_int64, C.c_int32, vp, vp]),
+        "mcc_pair": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                               C.c_uint64, vp, vp, vp, vp]),
+        "mcc_scatter": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), P(C.c_double),
+                                  C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, P(_Params), vp, vp]),
+        "mcc_correct": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), C.c_int32,
+                                  C.c_int32, C.c_int32, P(_Params), vp, vp, vp, vp]),
+        "mcc_step_workspace_size": (C.c_int, [vp, C.c_int32, C.c_int32, P(C.c_size_t)]),
+        "mcc_step_fused": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), P(C.c_double),
+                                     P(C.c_int32), C.c_int32, P(_Params), C.c_int32, C.c_int32, vp, vp, vp,
+                                     C.c_size_t, vp]),
+        "mcc_set_tile_cap": (C.c_int, [vp, C.c_int32]),
+        "mcc_sync_status": (C.c_int, [vp, vp]),
+        "mcc_launch_count": (C.c_int64, [vp]),
+        "mcc_status_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise MccError(rc, what)
+
+
+class Context:
+    """An ``mcc_ctx`` on one device (status word, work-queue counter) plus cached workspaces."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        _check(lib().mcc_create(C.byref(h), self.device), "mcc_create")
+        self.handle = h
+        self._ws = {}
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().mcc_destroy(self.handle)
+        except Exception:
+            pass
+
+    def workspace(self, key, nbytes: int) -> torch.Tensor | None:
+        if nbytes == 0:
+            return None
+        t = self._ws.get(key)
+        if t is None or t.numel() < nbytes:
+            t = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._ws[key] = t
+        return t
+
+    def launch_count(self) -> int:
+        return int(lib().mcc_launch_count(self.handle))
+
+    def set_tile_cap(self, cap: int):
+        _check(lib().mcc_set_tile_cap(self.handle, int(cap)), "mcc_set_tile_cap")
+
+    def sync_status(self, stream=None) -> int:
+        return int(lib().mcc_sync_status(self.handle, _stream(stream, self.device)))
+
+
+_CTX: dict[int, Context] = {}
+
+
+def context(device: int | torch.device | None = None) -> Context:
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    if dev not in _CTX:
+        _CTX[dev] = Context(dev)
+    return _CTX[dev]
+
+
+def _stream(stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _particles(vx, vy, vz, w) -> _Particles:
+    if vx.dtype == torch.float64:
+        prec = F64
+    elif vx.dtype == torch.float32:
+        prec = F32_MIXED
+    else:
+        raise TypeError("velocities must be float64 or float32")
+    for t in (vx, vy, vz):
+        if t.dtype != vx.dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != vx.numel():
+            raise TypeError("vx, vy, vz must be contiguous CUDA tensors of one dtype and length")
+    if w.dtype != torch.float64 or not w.is_cuda or not w.is_contiguous() or w.numel() != vx.numel():
+        raise TypeError("w must be a contiguous float64 CUDA tensor of the particles' length")
+    return _Particles(vx.data_ptr(), vy.data_ptr(), vz.data_ptr(), w.data_ptr(), vx.numel(), prec)
+
+
+def _species(species) -> C.Array:
+    arr = (_Species * len(species))()
+    for k, (q, m) in enumerate(species):
+        arr[k] = _Species(float(q), float(m))
+    return arr
+
+
+def _lnL(lnL, S: int):
+    import numpy as np
+    L = np.asarray(lnL, dtype=np.float64)
+    if L.ndim == 0:
+        L = np.full((S, S), float(L))
+    L = np.ascontiguousarray(L.reshape(S, S))
+    return (C.c_double * (S * S))(*L.reshape(-1).tolist())
+
+
+# ---------------------------------------------------------------------------------------------------- C-ABI calls
+def mcc_bin(cell: torch.Tensor, species: torch.Tensor, n_cells: int, n_species: int, stream=None):
+    """Stable counting sort by (cell, species); returns (perm int32[n], offsets int64[n_cells*n_species+1])."""
+    ctx = context(cell.device)
+    n = cell.numel()
+    perm = torch.empty(n, dtype=torch.int32, device=cell.device)
+    offsets = torch.empty(n_cells * n_species + 1, dtype=torch.int64, device=cell.device)
+    nb = C.c_size_t()
+    _check(lib().mcc_bin_workspace_size(n, n_cells, n_species, C.byref(nb)), "mcc_bin_workspace_size")
+    ws = ctx.workspace("bin", nb.value)
+    _check(lib().mcc_bin(ctx.handle, _ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
+                         _ptr(ws), nb.value, _stream(stream, cell.device)), "mcc_bin")
+    return perm, offsets
+
+
+def mcc_gather(x: torch.Tensor, perm: torch.Tensor, stream=None) -> torch.Tensor:
+    out = torch.empty_like(x)
+    _check(lib().mcc_gather(_ptr(x), _ptr(perm), x.numel(), x.element_size(), _ptr(out),
+                            _stream(stream, x.device)), "mcc_gather")
+    return out
+
+
+def mcc_pair(offsets: torch.Tensor, n_cells: int, n_species: int, sa: int, sb: int, inter: int, seed: int,
+             step: int, stream=None):
+    """Takizuka-Abe pairs of interaction (sa, sb); returns (pair_i, pair_j, flags), each of length N."""
+    ctx = context(offsets.device)
+    N = int(offsets[-1].item())
+    pi = torch.full((max(N, 1),), -1, dtype=torch.int32, device=offsets.device)
+    pj = torch.full((max(N, 1),), -1, dtype=torch.int32, device=offsets.device)
+    fl = torch.zeros(max(N, 1), dtype=torch.uint8, device=offsets.device)
+    _check(lib().mcc_pair(ctx.handle, _ptr(offsets), n_cells, n_species, sa, sb, inter, seed & (2**64 - 1),
+                          step & (2**64 - 1), _ptr(pi), _ptr(pj), _ptr(fl), _stream(stream, offsets.device)),
+           "mcc_pair")
+    return pi[:N], pj[:N], fl[:N]
+
+
+def mcc_scatter(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, sa, sb, inter, pairs, params: Params,
+                stream=None) -> torch.Tensor:
+    """Pair loop of interaction (sa, sb) in place; returns the pre-scatter copy (3, N)."""
+    ctx = context(vx.device)
+    P = _particles(vx, vy, vz, w)
+    backup = torch.empty((3, max(vx.numel(), 1)), dtype=vx.dtype, device=vx.device)
+    pi, pj, fl = pairs
+    cp = params._c()
+    _check(lib().mcc_scatter(ctx.handle, C.byref(P), _ptr(offsets), n_cells, n_species, _species(species),
+                             _lnL(lnL, n_species), sa, sb, inter, _ptr(pi), _ptr(pj), _ptr(fl), C.byref(cp),
+                             _ptr(backup), _stream(stream, vx.device)), "mcc_scatter")
+    return backup[:, : vx.numel()]
+
+
+def mcc_correct(vx, vy, vz, w, offsets, n_cells, n_species, species, sa, sb, inter, params: Params,
+                backup: torch.Tensor, stream=None):
+    """Moment correction of interaction (sa, sb) in place; returns (corr_pairs, fail_flags) per cell."""
+    ctx = context(vx.device)
+    P = _particles(vx, vy, vz, w)
+    bk = backup.contiguous()
+    if bk.dim() != 2 or bk.shape[0] != 3 or bk.dtype != vx.dtype:
+        raise TypeError("backup must be the (3, N) tensor returned by mcc_scatter")
+    corr = torch.zeros(max(n_cells, 1), dtype=torch.int32, device=vx.device)
+    fail = torch.zeros(max(n_cells, 1), dtype=torch.int32, device=vx.device)
+    cp = params._c()
+    _check(lib().mcc_correct(ctx.handle, C.byref(P), _ptr(offsets), n_cells, n_species, _species(species), sa, sb,
+                             inter, C.byref(cp), _ptr(bk), _ptr(corr), _ptr(fail), _stream(stream, vx.device)),
+           "mcc_correct")
+    return corr[:n_cells], fail[:n_cells]
+
+
+def default_interactions(n_species: int):
+    return [(a, b) for a in range(n_species) for b in range(a, n_species)]
+
+
+def mcc_step_fused(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, params: Params, n_steps: int = 1,
+                   max_cell: int | None = None, interactions=None, corr_pairs=None, fail_count=None, stream=None):
+    """n_steps whole collision steps in place (one persistent kernel launch per step). Returns the per-cell
+    accumulated (corr_pairs, fail_count) tensors."""
+    ctx = context(vx.device)
+    P = _particles(vx, vy, vz, w)
+    inter = default_interactions(n_species) if interactions is None else [tuple(x) for x in interactions]
+    flat = (C.c_int32 * (2 * len(inter)))(*[int(v) for ab in inter for v in ab])
+    if max_cell is None:
+        max_cell = int((offsets[n_species::n_species] - offsets[:-1:n_species]).max().item()) if n_cells else 0
+    if corr_pairs is None:
+        corr_pairs = torch.zeros(max(n_cells, 1), dtype=torch.int32, device=vx.device)
+    if fail_count is None:
+        fail_count = torch.zeros(max(n_cells, 1), dtype=torch.int32, device=vx.device)
+    nb = C.c_size_t()
+    _check(lib().mcc_step_workspace_size(ctx.handle, P.prec, int(max_cell), C.byref(nb)), "mcc_step_workspace_size")
+    ws = ctx.workspace(("step", P.prec), nb.value)
+    cp = params._c()
+    _check(lib().mcc_step_fused(ctx.handle, C.byref(P), _ptr(offsets), n_cells, n_species, _species(species),
+                                _lnL(lnL, n_species), flat, len(inter), C.byref(cp), int(n_steps), int(max_cell),
+                                _ptr(corr_pairs), _ptr(fail_count), _ptr(ws), nb.value,
+                                _stream(stream, vx.device)), "mcc_step_fused")
+    return corr_pairs[:n_cells], fail_count[:n_cells]
+
+
+def sync_status(device=None, stream=None):
+    """Synchronise and raise MccError if the device latched an error since the last check."""
+    ctx = context(device)
+    rc = ctx.sync_status(stream)
+    _check(rc, "device status")

@@ -1,0 +1,369 @@
+// C ABI of the collision step (declarations and contracts in include/mcc.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/mcc.h"
+#include "mcc_kernels.h"
+
+struct mcc_ctx {
+    int device;
+    int32_t* dbuf;  // [0] status word, [1] work-queue counter
+    int64_t launches;
+    int num_sms;
+    size_t smem_optin;
+    int32_t tile_cap;  // particles staged on chip per cell; 0 = automatic
+};
+
+namespace {
+
+using mcc::StepArgs;
+
+constexpr size_t kStaticSmemReserve = 2048;  // Shared struct of the cell kernel plus margin
+constexpr int kAutoTileCap = 2048;           // default on-chip tile when cells are larger
+constexpr int kMaxCtasPerSm = 2048 / mcc::kThreads;
+
+cudaStream_t S(mcc_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MCC_OK : MCC_ERR_CUDA; }
+
+bool valid_params(const mcc_params* p)
+{
+    if (!p) return false;
+    if (p->method != MCC_TA77 && p->method != MCC_N97) return false;
+    if (!(p->dt > 0) || !(p->dV > 0) || !(p->eps0 > 0) || !(p->fE > 0) || !(p->fE < 1)) return false;
+    if (p->relativistic && !(p->c > 0)) return false;
+    if (p->max_corr_passes < 0 || p->fail_policy < 0 || p->fail_policy > 2) return false;
+    return true;
+}
+
+// Fill the species / interaction constants of a launch (host FP64; one rounding to float for the mixed path).
+int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells,
+              int32_t n_species, const mcc_species* sp, const double* lnL, const int32_t* inter, int32_t n_inter,
+              int32_t inter_base, const mcc_params* p)
+{
+    std::memset(&a, 0, sizeof a);
+    if (n_species < 1 || n_species > mcc::kMaxSpecies || n_cells < 0 || n_inter < 1 || n_inter > mcc::kMaxInter)
+        return MCC_ERR_INVALID_ARG;
+    a.offsets = offsets;
+    a.n_cells = n_cells;
+    a.S = n_species;
+    if (P) {
+        a.vx = P->vx;
+        a.vy = P->vy;
+        a.vz = P->vz;
+        a.w = P->w;
+        a.n_total = P->n;
+    }
+    if (sp) {
+        for (int s = 0; s < n_species; ++s) {
+            if (!(sp[s].m > 0)) return MCC_ERR_INVALID_ARG;
+            a.m[s] = sp[s].m;
+            a.m_f[s] = (float)sp[s].m;
+            a.ma[s] = sp[s].m;
+            a.ma_f[s] = (float)sp[s].m;
+        }
+    }
+    for (int k = 0; k < n_inter; ++k) {
+        const int ia = inter[2 * k], ib = inter[2 * k + 1];
+        if (ia < 0 || ib < ia || ib >= n_species) return MCC_ERR_INVALID_ARG;
+        mcc::InterConst& ic = a.ic[k];
+        ic.a = ia;
+        ic.b = ib;
+        if (sp && lnL && p) {
+            const double qa = sp[ia].q, qb = sp[ib].q, ma = sp[ia].m, mb = sp[ib].m;
+            const double mu = ma * mb / (ma + mb);
+            const double L = lnL[ia * n_species + ib];
+            const double kappa = qa * qa * qb * qb * L * p->dt / (4.0 * M_PI * p->eps0 * p->eps0 * p->dV);
+            ic.kappa = kappa;
+            ic.kappa_mu2 = kappa / (mu * mu);
+            ic.mu_ma = mu / ma;
+            ic.mu_mb = mu / mb;
+            ic.kappa_f = (float)ic.kappa;
+            ic.kappa_mu2_f = (float)ic.kappa_mu2;
+            ic.mu_ma_f = (float)ic.mu_ma;
+            ic.mu_mb_f = (float)ic.mu_mb;
+        }
+    }
+    a.n_inter = n_inter;
+    a.inter_base = inter_base;
+    if (p) {
+        a.method = p->method;
+        a.fail_policy = p->fail_policy;
+        a.sort_by_weight = p->sort_by_weight;
+        a.max_corr_passes = p->max_corr_passes;
+        a.correct = p->correct;
+        a.c = p->c;
+        a.fE = p->fE;
+        a.c_f = (float)p->c;
+        a.fE_f = (float)p->fE;
+        a.rng.k0 = (uint32_t)p->seed;
+        a.rng.k1 = (uint32_t)(p->seed >> 32);
+        a.rng.step = (uint32_t)p->step;
+    }
+    a.status = ctx->dbuf;
+    a.queue = ctx->dbuf + 1;
+    return MCC_OK;
+}
+
+size_t max_tile_particles(const mcc_ctx* ctx, bool f32)
+{
+    const size_t avail = ctx->smem_optin > kStaticSmemReserve ? ctx->smem_optin - kStaticSmemReserve : 0;
+    return avail / mcc::tile_bytes_per_particle(f32);
+}
+
+// Launch one cell-kernel pass over every cell (queue reset, persistent grid of at most max_grid CTAs).
+int run_cells(mcc_ctx* ctx, StepArgs& a, bool f32, bool rel, int mode, int cap, cudaStream_t st,
+              int max_grid = 1 << 30)
+{
+    const size_t smem = (size_t)cap * mcc::tile_bytes_per_particle(f32);
+    if (mcc::set_cell_smem_limit(f32, rel, mode, smem) != cudaSuccess) return MCC_ERR_CUDA;
+    int bps = mcc::cell_kernel_blocks_per_sm(f32, rel, mode, smem);
+    if (bps < 1) return MCC_ERR_CUDA;
+    int grid = ctx->num_sms * bps;
+    if (grid > max_grid) grid = max_grid;
+    if (a.n_cells < grid) grid = a.n_cells > 0 ? a.n_cells : 1;
+    a.cap = cap;
+    cudaError_t e = cudaMemsetAsync(ctx->dbuf + 1, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return MCC_ERR_CUDA;
+    e = mcc::launch_cell(f32, rel, mode, a, grid, smem, st);
+    ctx->launches += 1;
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcc_create(mcc_ctx** out, int device)
+{
+    if (!out) return MCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    mcc_ctx* c = new (std::nothrow) mcc_ctx();
+    if (!c) return MCC_ERR_CUDA;
+    c->device = device;
+    c->launches = 0;
+    c->tile_cap = 0;
+    int optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    c->smem_optin = (size_t)optin;
+    c->num_sms = sms;
+    if (cudaMalloc(&c->dbuf, 64) != cudaSuccess || cudaMemset(c->dbuf, 0, 64) != cudaSuccess) {
+        delete c;
+        return MCC_ERR_CUDA;
+    }
+    *out = c;
+    return MCC_OK;
+}
+
+void mcc_destroy(mcc_ctx* ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaFree(ctx->dbuf);
+    delete ctx;
+}
+
+int mcc_bin_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t* bytes)
+{
+    if (!bytes || n < 0 || n_cells <= 0 || n_species <= 0) return MCC_ERR_INVALID_ARG;
+    *bytes = mcc::bin_workspace_bytes(n, (int64_t)n_cells * n_species);
+    return MCC_OK;
+}
+
+int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
+            int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws, size_t ws_bytes, mcc_stream stream)
+{
+    if (!ctx || n < 0 || n_cells <= 0 || n_species <= 0 || !offsets_out) return MCC_ERR_INVALID_ARG;
+    if (n > 0 && (!cell || !species || !perm_out)) return MCC_ERR_INVALID_ARG;
+    if (n > INT32_MAX) return MCC_ERR_TOO_LARGE;
+    if (!ws || ws_bytes < mcc::bin_workspace_bytes(n, (int64_t)n_cells * n_species)) return MCC_ERR_WORKSPACE;
+    DeviceGuard g(ctx->device);
+    return cuda_status(mcc::launch_bin(cell, species, n, n_cells, n_species, perm_out, offsets_out, ws, ctx->dbuf,
+                                       S(stream), &ctx->launches));
+}
+
+int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream)
+{
+    if (n < 0 || (elem_bytes != 4 && elem_bytes != 8) || (n > 0 && (!in || !perm || !out))) return MCC_ERR_INVALID_ARG;
+    return cuda_status(mcc::launch_gather(in, perm, n, elem_bytes, out, S(stream)));
+}
+
+int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_species, int32_t sa, int32_t sb,
+             int32_t inter, uint64_t seed, uint64_t step, int32_t* pair_i, int32_t* pair_j, uint8_t* pair_flags,
+             mcc_stream stream)
+{
+    if (!ctx || !offsets || !pair_i || !pair_j || !pair_flags || inter < 0 || inter > 0xFFFFFF)
+        return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    StepArgs a;
+    const int32_t ab[2] = {sa, sb};
+    mcc_params p;
+    std::memset(&p, 0, sizeof p);
+    p.seed = seed;
+    p.step = step;
+    int rc = fill_args(a, ctx, nullptr, offsets, n_cells, n_species, nullptr, nullptr, ab, 1, inter, &p);
+    if (rc != MCC_OK) return rc;
+    if (n_cells == 0) return MCC_OK;
+    a.pair_i = pair_i;
+    a.pair_j = pair_j;
+    a.pair_flags = pair_flags;
+    const int cap = (int)max_tile_particles(ctx, false);
+    return run_cells(ctx, a, false, false, mcc::kPair, cap, S(stream));
+}
+
+int mcc_scatter(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells, int32_t n_species,
+                const mcc_species* sp, const double* lnL, int32_t sa, int32_t sb, int32_t inter, const int32_t* pair_i,
+                const int32_t* pair_j, const uint8_t* pair_flags, const mcc_params* p, void* backup,
+                mcc_stream stream)
+{
+    if (!ctx || !P || !offsets || !sp || !lnL || !pair_i || !pair_j || !pair_flags || !backup || !valid_params(p) ||
+        inter < 0 || inter > 0xFFFFFF)
+        return MCC_ERR_INVALID_ARG;
+    if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    StepArgs a;
+    const int32_t ab[2] = {sa, sb};
+    int rc = fill_args(a, ctx, P, offsets, n_cells, n_species, sp, lnL, ab, 1, inter, p);
+    if (rc != MCC_OK) return rc;
+    if (n_cells == 0) return MCC_OK;
+    a.pair_i = const_cast<int32_t*>(pair_i);
+    a.pair_j = const_cast<int32_t*>(pair_j);
+    a.pair_flags = const_cast<uint8_t*>(pair_flags);
+    a.backup = backup;
+    const bool f32 = P->prec == MCC_F32_MIXED;
+    const int cap = (int)max_tile_particles(ctx, f32);
+    return run_cells(ctx, a, f32, p->relativistic != 0, mcc::kScatter, cap, S(stream));
+}
+
+int mcc_correct(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells, int32_t n_species,
+                const mcc_species* sp, int32_t sa, int32_t sb, int32_t inter, const mcc_params* p,
+                const void* backup, int32_t* corr_pairs_out, int32_t* fail_flags_out, mcc_stream stream)
+{
+    if (!ctx || !P || !offsets || !sp || !backup || !valid_params(p) || inter < 0 || inter > 0xFFFFFF)
+        return MCC_ERR_INVALID_ARG;
+    if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    StepArgs a;
+    const int32_t ab[2] = {sa, sb};
+    int rc = fill_args(a, ctx, P, offsets, n_cells, n_species, sp, nullptr, ab, 1, inter, p);
+    if (rc != MCC_OK) return rc;
+    if (n_cells == 0) return MCC_OK;
+    a.backup = const_cast<void*>(backup);
+    a.corr_pairs = corr_pairs_out;
+    a.fail_count = fail_flags_out;
+    const bool f32 = P->prec == MCC_F32_MIXED;
+    const int cap = (int)max_tile_particles(ctx, f32);
+    return run_cells(ctx, a, f32, p->relativistic != 0, mcc::kCorrect, cap, S(stream));
+}
+
+int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t max_cell, size_t* bytes)
+{
+    if (!ctx || !bytes || max_cell < 0 || (prec != MCC_F64 && prec != MCC_F32_MIXED)) return MCC_ERR_INVALID_ARG;
+    const bool f32 = prec == MCC_F32_MIXED;
+    const size_t capmax = max_tile_particles(ctx, f32);
+    const int tile = ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
+                                       : (int)((size_t)kAutoTileCap < capmax ? (size_t)kAutoTileCap : capmax);
+    if (max_cell <= tile) {
+        *bytes = 0;
+        return MCC_OK;
+    }
+    const size_t stride = ((size_t)max_cell * mcc::tile_bytes_per_particle(f32) + 255) & ~(size_t)255;
+    // one slab per resident CTA (at most kMaxCtasPerSm per SM) for the cells larger than the on-chip tile
+    *bytes = stride * (size_t)ctx->num_sms * kMaxCtasPerSm;
+    return MCC_OK;
+}
+
+int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells, int32_t n_species,
+                   const mcc_species* sp, const double* lnL, const int32_t* interactions, int32_t n_inter,
+                   const mcc_params* p, int32_t n_steps, int32_t max_cell, int32_t* corr_pairs, int32_t* fail_count,
+                   void* ws, size_t ws_bytes, mcc_stream stream)
+{
+    if (!ctx || !P || !offsets || !sp || !lnL || !interactions || !valid_params(p) || n_steps < 0 || max_cell < 0)
+        return MCC_ERR_INVALID_ARG;
+    if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    StepArgs a;
+    int rc = fill_args(a, ctx, P, offsets, n_cells, n_species, sp, lnL, interactions, n_inter, 0, p);
+    if (rc != MCC_OK) return rc;
+    if (n_cells == 0 || n_steps == 0) return MCC_OK;
+    a.corr_pairs = corr_pairs;
+    a.fail_count = fail_count;
+    const bool f32 = P->prec == MCC_F32_MIXED;
+    const bool rel = p->relativistic != 0;
+    const size_t capmax = max_tile_particles(ctx, f32);
+    const int tile = ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
+                                       : (int)((size_t)kAutoTileCap < capmax ? (size_t)kAutoTileCap : capmax);
+    const int cap = max_cell <= tile ? (max_cell > 0 ? max_cell : 1) : tile;
+    int max_grid = 1 << 30;
+    if (max_cell > tile) {
+        size_t need = 0;
+        mcc_step_workspace_size(ctx, P->prec, max_cell, &need);
+        if (!ws || ws_bytes < need) return MCC_ERR_WORKSPACE;
+        a.slab = reinterpret_cast<char*>(ws);
+        a.slab_stride = (int64_t)(((size_t)max_cell * mcc::tile_bytes_per_particle(f32) + 255) & ~(size_t)255);
+        a.slab_cap = max_cell;
+        max_grid = (int)(ws_bytes / (size_t)a.slab_stride);
+    }
+    for (int32_t t = 0; t < n_steps; ++t) {
+        a.rng.step = (uint32_t)(p->step + (uint64_t)t);
+        rc = run_cells(ctx, a, f32, rel, mcc::kFused, cap, S(stream), max_grid);
+        if (rc != MCC_OK) return rc;
+    }
+    return MCC_OK;
+}
+
+int mcc_sync_status(mcc_ctx* ctx, mcc_stream stream)
+{
+    if (!ctx) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
+    int32_t st = 0;
+    if (cudaMemcpy(&st, ctx->dbuf, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return MCC_ERR_CUDA;
+    if (cudaMemset(ctx->dbuf, 0, sizeof(int32_t)) != cudaSuccess) return MCC_ERR_CUDA;
+    return st;
+}
+
+int64_t mcc_launch_count(mcc_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int mcc_set_tile_cap(mcc_ctx* ctx, int32_t cap)
+{
+    if (!ctx || cap < 0) return MCC_ERR_INVALID_ARG;
+    ctx->tile_cap = cap;
+    return MCC_OK;
+}
+
+const char* mcc_status_string(int status)
+{
+    switch (status) {
+    case MCC_OK: return "ok";
+    case MCC_ERR_INVALID_ARG: return "invalid argument";
+    case MCC_ERR_CUDA: return "CUDA error";
+    case MCC_ERR_WORKSPACE: return "workspace missing or too small";
+    case MCC_ERR_TIMEOUT: return "bounded wait timed out";
+    case MCC_ERR_CORRECTION_FAILED: return "energy correction could not absorb the violation";
+    case MCC_ERR_BOUNDS: return "index or cell size out of bounds";
+    case MCC_ERR_TOO_LARGE: return "segment larger than supported";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Cell binning: stable counting sort of particles by key = cell * S + species (particles collide per cell of
+// volume dV, Sec. 2), and a gather through the resulting permutation.
+//
+// histogram (atomic counts) -> exclusive scan -> scatter with atomic cursors (order within a segment arbitrary)
+// -> per-segment sort of the particle indices, which restores the stable (index) order. The result does not depend
+// on the order in which the atomics were served.
+#include "mcc_kernels.h"
+
+namespace mcc {
+namespace {
+
+constexpr int kBinThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kSegCap = 12288;  // indices sorted in shared memory per segment; larger segments sort in place
+
+__global__ void k_hist(const int32_t* __restrict__ cell, const int32_t* __restrict__ species, int64_t n,
+                       int32_t n_cells, int32_t S, int32_t* __restrict__ counts, int32_t* status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cell[i], s = species[i];
+        if (c < 0 || c >= n_cells || s < 0 || s >= S) {
+            latch(status, kErrBounds);
+            continue;
+        }
+        atomicAdd(&counts[(int64_t)c * S + s], 1);
+    }
+}
+
+// Exclusive scan of nk counts into nk + 1 offsets by one CTA: per-thread contiguous chunks, a scan of the chunk
+// totals in shared memory, then each chunk writes its offsets.
+__global__ void __launch_bounds__(kScanThreads) k_scan(const int32_t* __restrict__ counts, int64_t nk,
+                                                       int64_t* __restrict__ offsets, int32_t* status)
+{
+    __shared__ int64_t part[kScanThreads];
+    const int64_t chunk = (nk + kScanThreads - 1) / kScanThreads;
+    const int64_t b = (int64_t)threadIdx.x * chunk;
+    const int64_t e = b + chunk < nk ? b + chunk : nk;
+    int64_t s = 0;
+    for (int64_t k = b; k < e; ++k) {
+        const int32_t x = counts[k];
+        if (x > (1 << kPermBits)) latch(status, kErrTooLarge);
+        s += x;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        const int64_t y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - s;
+    for (int64_t k = b; k < e; ++k) {
+        offsets[k] = run;
+        run += counts[k];
+    }
+    if (threadIdx.x == kScanThreads - 1) offsets[nk] = part[kScanThreads - 1];
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ cell, const int32_t* __restrict__ species, int64_t n,
+                          int32_t n_cells, int32_t S, const int64_t* __restrict__ offsets,
+                          int32_t* __restrict__ cursor, int32_t* __restrict__ perm)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cell[i], s = species[i];
+        if (c < 0 || c >= n_cells || s < 0 || s >= S) continue;
+        const int64_t key = (int64_t)c * S + s;
+        perm[offsets[key] + atomicAdd(&cursor[key], 1)] = (int32_t)i;
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_segsort(const int64_t* __restrict__ offsets, int64_t nk,
+                                                         int32_t* __restrict__ perm)
+{
+    __shared__ int32_t buf[kSegCap];
+    for (int64_t seg = blockIdx.x; seg < nk; seg += gridDim.x) {
+        const int64_t b = offsets[seg];
+        const int n = (int)(offsets[seg + 1] - b);
+        if (n < 2) continue;
+        if (n <= kSegCap) {
+            for (int i = threadIdx.x; i < n; i += kBinThreads) buf[i] = perm[b + i];
+            __syncthreads();
+            block_sort_i32(buf, n);
+            for (int i = threadIdx.x; i < n; i += kBinThreads) perm[b + i] = buf[i];
+        } else {
+            block_sort_i32(perm + b, n);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void k_gather(const T* __restrict__ in, const int32_t* __restrict__ perm, int64_t n, T* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = in[perm[k]];
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * 16;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace
+
+size_t bin_workspace_bytes(int64_t n, int64_t n_keys)
+{
+    (void)n;
+    const size_t one = ((size_t)n_keys * sizeof(int32_t) + 255) & ~(size_t)255;
+    return 2 * one;
+}
+
+cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
+                       int32_t* perm, int64_t* offsets, void* ws, int32_t* status, cudaStream_t st, int64_t* launches)
+{
+    const int64_t nk = (int64_t)n_cells * n_species;
+    const size_t one = ((size_t)nk * sizeof(int32_t) + 255) & ~(size_t)255;
+    int32_t* counts = reinterpret_cast<int32_t*>(ws);
+    int32_t* cursor = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) + one);
+    cudaError_t e = cudaMemsetAsync(ws, 0, 2 * one, st);
+    if (e != cudaSuccess) return e;
+    const int g = grid_for(n, kBinThreads);
+    if (n > 0) k_hist<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, counts, status);
+    k_scan<<<1, kScanThreads, 0, st>>>(counts, nk, offsets, status);
+    if (n > 0) {
+        k_scatter<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, offsets, cursor, perm);
+        const int gs = grid_for(nk * kBinThreads, kBinThreads);
+        k_segsort<<<gs, kBinThreads, 0, st>>>(offsets, nk, perm);
+        *launches += 3;
+    }
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* in, const int32_t* perm, int64_t n, int elem_bytes, void* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int g = grid_for(n, kBinThreads);
+    if (elem_bytes == 8)
+        k_gather<uint64_t><<<g, kBinThreads, 0, st>>>(reinterpret_cast<const uint64_t*>(in), perm, n,
+                                                      reinterpret_cast<uint64_t*>(out));
+    else
+        k_gather<uint32_t><<<g, kBinThreads, 0, st>>>(reinterpret_cast<const uint32_t*>(in), perm, n,
+                                                      reinterpret_cast<uint32_t*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace mcc

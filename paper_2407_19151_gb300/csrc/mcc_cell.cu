@@ -1,0 +1,720 @@
+// Cell kernel of the weighted, moment-preserving Monte-Carlo Coulomb collision step.
+//
+// One CTA owns one cell at a time (persistent CTAs pull cells from an atomic work queue). The cell's particles are
+// staged in shared memory as a tile: velocities, their pre-interaction copy, weights, sort keys and the random
+// permutation. For every interaction (a, b) of the step it then runs Algorithm 1 of the paper:
+//   random permutation(s) (Philox keys, bitonic sort)  -> Takizuka-Abe pairs (Sec. 3.2, Fig. TApairing)
+//   pair loop: weighted scattering length (Eq. sab_TA77), TA77 / N97 angle, rotation, rejection of the heavier
+//              particle with probability 1 - w_min/w_max (Sec. 3.2); inter-species pairs in rounds of N_min
+//              disjoint pairs, rounds in order
+//   momentum shift (Eq. vp_pm), energy violation (Eq. Econs), split (Eq. DeltaEs), optional weight sort,
+//   energy-correction pairs (Eqs. vp1_inelastic, vp2_inelastic, vrel_inelastic, U_inelastic; Appendix A) as a
+//   block-wide prefix sum over the pair caps fE * KE_cm, failure fallback (Sec. 5.2).
+// The unfused C-ABI calls run single phases of the same code: PAIR writes the pair list, SCATTER the pair loop
+// (reading the list, writing the pre-scatter copy), CORRECT the moment correction (reading that copy).
+//
+// FP64 path: everything in double. Mixed path: float velocities and kinematics, float-float accumulation of the
+// per-cell sums, FP64 only for the per-cell coefficients (B, Delta E, its split) computed by one thread.
+#include "mcc_kernels.h"
+
+namespace mcc {
+namespace {
+
+template <class V>
+struct WStore;
+template <>
+struct WStore<double> {
+    using T = double;
+};
+template <>
+struct WStore<float> {
+    using T = float2;  // (hi, lo) split of the double weight
+};
+
+template <class V>
+struct Tile {
+    uint64_t* keys;
+    typename WStore<V>::T* w;
+    V* v;   // [3][cap]
+    V* vb;  // [3][cap] pre-interaction copy
+    int32_t* perm;
+    int cap;
+};
+
+template <class V>
+__device__ __forceinline__ Tile<V> make_tile(unsigned char* base, int cap)
+{
+    Tile<V> t;
+    t.cap = cap;
+    t.keys = reinterpret_cast<uint64_t*>(base);
+    t.w = reinterpret_cast<typename WStore<V>::T*>(base + 8 * (size_t)cap);
+    t.v = reinterpret_cast<V*>(base + 16 * (size_t)cap);
+    t.vb = t.v + 3 * (size_t)cap;
+    t.perm = reinterpret_cast<int32_t*>(base + (16 + 6 * sizeof(V)) * (size_t)cap);
+    return t;
+}
+
+__device__ __forceinline__ double wv(const Tile<double>& t, int i) { return t.w[i]; }
+__device__ __forceinline__ float wv(const Tile<float>& t, int i) { return t.w[i].x; }
+__device__ __forceinline__ bool w_equal(const Tile<double>& t, int i, int j) { return t.w[i] == t.w[j]; }
+__device__ __forceinline__ bool w_equal(const Tile<float>& t, int i, int j)
+{
+    return t.w[i].x == t.w[j].x && t.w[i].y == t.w[j].y;
+}
+__device__ __forceinline__ double w_exact(const Tile<double>& t, const StepArgs&, int64_t, int i) { return t.w[i]; }
+__device__ __forceinline__ double w_exact(const Tile<float>&, const StepArgs& A, int64_t cs, int i)
+{
+    return A.w[cs + i];
+}
+__device__ __forceinline__ void w_store(Tile<double>& t, int i, double w) { t.w[i] = w; }
+__device__ __forceinline__ void w_store(Tile<float>& t, int i, double w) { t.w[i] = split_weight(w); }
+
+template <class V>
+__device__ __forceinline__ V pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+struct Shared {
+    int off[kMaxSpecies + 1];
+    int cell;
+    int fail;
+    double red[kWarps * 8 + 8];
+    double scan_d[kWarps + 1];
+    float scan_f[kWarps + 1];
+    int iscr[kWarps];
+    double B[3];
+    float Bf[3];
+    double D[2];
+};
+
+template <class V>
+__device__ __forceinline__ V* scan_scratch(Shared& sh);
+template <>
+__device__ __forceinline__ double* scan_scratch<double>(Shared& sh) { return sh.scan_d; }
+template <>
+__device__ __forceinline__ float* scan_scratch<float>(Shared& sh) { return sh.scan_f; }
+
+// k-th Takizuka-Abe pair of the interaction (cell-local indices). See mcc_pair in mcc.h for the rule.
+template <class V>
+__device__ __forceinline__ void pair_at(const Tile<V>& t, bool intra, int na, int nb, int a0, int b0, int p, int& i,
+                                        int& j, uint8_t& f)
+{
+    f = 0;
+    if (intra) {
+        if (na & 1) {
+            if (p < 3) {
+                i = t.perm[a0 + p];
+                j = t.perm[a0 + (p + 1) % 3];
+                f = kPairTriplet;
+                return;
+            }
+            i = t.perm[a0 + 2 * p - 3];
+            j = t.perm[a0 + 2 * p - 2];
+            return;
+        }
+        i = t.perm[a0 + 2 * p];
+        j = t.perm[a0 + 2 * p + 1];
+        return;
+    }
+    if (na >= nb) {
+        i = t.perm[a0 + p];
+        j = t.perm[b0 + p % nb];
+    } else {
+        i = t.perm[a0 + p % na];
+        j = t.perm[b0 + p];
+    }
+}
+
+// Heavier particle of an unequal-weight pair moves iff U3 w_max < w_min, decided in FP64 exactly as the
+// definition states. The mixed path first decides in float with a bound on the float error and falls back to the
+// FP64 test only within that bound of the boundary.
+__device__ __forceinline__ bool heavy_moves(const Tile<double>& t, const StepArgs&, int64_t, int i, int j,
+                                            uint32_t r)
+{
+    const double U3 = u23<double>(r);
+    const double wi = t.w[i], wj = t.w[j];
+    return U3 * fmax(wi, wj) < fmin(wi, wj);
+}
+
+__device__ __forceinline__ bool heavy_moves(const Tile<float>& t, const StepArgs& A, int64_t cs, int i, int j,
+                                            uint32_t r)
+{
+    const float U3 = u23<float>(r);
+    const float hi_i = t.w[i].x, hi_j = t.w[j].x;
+    const float p = U3 * fmaxf(hi_i, hi_j);
+    const float wmin = fminf(hi_i, hi_j);
+    const float x = p - wmin;
+    const float tol = 10.0f * 5.9604645e-8f * fmaxf(p, wmin);
+    if (x > tol) return false;
+    if (x < -tol) return true;
+    const double wi = A.w[cs + i], wj = A.w[cs + j];
+    return u23<double>(r) * fmax(wi, wj) < fmin(wi, wj);
+}
+
+// Relativistic pair, given its CM frame: scattering length with |p*|^2 v_rel* in place of mu^2 u^3, rotation of p*
+// through (Theta, phi), boost of the change back to the lab frame. Returns dp = p_i' - p_i.
+template <class V>
+__device__ __forceinline__ void rel_pair_dp_cm(const StepArgs& A, const InterConst& ic, const RelCM<V>& cm, V cc,
+                                               V wmax, int nmin, uint8_t f, V U1, V U2, V U4, V dp[3])
+{
+    V s = pick<V>(ic.kappa, ic.kappa_f) * wmax * (V)nmin / (cm.pmag * cm.pmag * cm.vrel);
+    if (f & kPairTriplet) s *= (V)0.5;
+    V st, omc, sp, cp, dx, dy, dz;
+    sample_angle<V>(A.method, s, U1, U4, st, omc);
+    sincospi_v((V)2 * U2, &sp, &cp);
+    rotate<V>(cm.px, cm.py, cm.pz, st, omc, cp, sp, dx, dy, dz);
+    const V coef_b = cm.gC * cm.gC / (cc * cc * (cm.gC + (V)1));
+    const V Vd = cm.Vx * dx + cm.Vy * dy + cm.Vz * dz;
+    dp[0] = dx + coef_b * Vd * cm.Vx;
+    dp[1] = dy + coef_b * Vd * cm.Vy;
+    dp[2] = dz + coef_b * Vd * cm.Vz;
+}
+
+template <class V>
+__device__ __noinline__ void rel_pair_dp(const StepArgs& A, const InterConst& ic, const V vi[3], const V vj[3],
+                                         V wmax, int nmin, uint8_t f, V U1, V U2, V U4, V dp[3])
+{
+    const V cc = pick<V>(A.c, A.c_f);
+    const V ma = pick<V>(A.ma[ic.a], A.ma_f[ic.a]), mb = pick<V>(A.ma[ic.b], A.ma_f[ic.b]);
+    const RelCM<V> cm = rel_cm<V>(cc, ma, mb, vi, vj);
+    if (!(cm.pmag > (V)0)) {
+        dp[0] = dp[1] = dp[2] = (V)0;
+        return;
+    }
+    rel_pair_dp_cm<V>(A, ic, cm, cc, wmax, nmin, f, U1, U2, U4, dp);
+}
+
+// One scattering pair (Algorithm 1 pair loop).
+template <class V, bool REL>
+__device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t, int c, int64_t cs, uint32_t ictr,
+                                             const InterConst& ic, int p, int i, int j, uint8_t f, int nmin)
+{
+    const int cap = t.cap;
+    V vi[3] = {t.v[i], t.v[cap + i], t.v[2 * cap + i]};
+    V vj[3] = {t.v[j], t.v[cap + j], t.v[2 * cap + j]};
+    const V wi = wv(t, i), wj = wv(t, j);
+    const V wmax = wi > wj ? wi : wj;
+    const uint4 r = draw(A.rng, (uint32_t)p, (uint32_t)c, ictr, kTagScat);
+    const V U1 = u23<V>(r.x), U2 = u23<V>(r.y), U4 = u23<V>(r.w);
+    V dvi[3], dvj[3];
+    if (!REL) {
+        const V ux = vi[0] - vj[0], uy = vi[1] - vj[1], uz = vi[2] - vj[2];
+        const V u2 = ux * ux + uy * uy + uz * uz;
+        if (u2 == (V)0) return;
+        const V um = sqrt(u2);
+        V s = pick<V>(ic.kappa_mu2, ic.kappa_mu2_f) * wmax * (V)nmin / (u2 * um);
+        if (f & kPairTriplet) s *= (V)0.5;
+        V st, omc, sp, cp, dx, dy, dz;
+        sample_angle<V>(A.method, s, U1, U4, st, omc);
+        sincospi_v((V)2 * U2, &sp, &cp);
+        rotate<V>(ux, uy, uz, st, omc, cp, sp, dx, dy, dz);
+        const V fa = pick<V>(ic.mu_ma, ic.mu_ma_f), fb = pick<V>(ic.mu_mb, ic.mu_mb_f);
+        dvi[0] = fa * dx; dvi[1] = fa * dy; dvi[2] = fa * dz;
+        dvj[0] = -fb * dx; dvj[1] = -fb * dy; dvj[2] = -fb * dz;
+    } else {
+        V du2 = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) du2 += (vi[d] - vj[d]) * (vi[d] - vj[d]);
+        if (du2 == (V)0) return;
+        const V cc = pick<V>(A.c, A.c_f);
+        const V ma = pick<V>(A.ma[ic.a], A.ma_f[ic.a]), mb = pick<V>(A.ma[ic.b], A.ma_f[ic.b]);
+        const RelCM<V> cm = rel_cm<V>(cc, ma, mb, vi, vj);
+        if (sizeof(V) == 4 && cm.gC > (V)2) {
+            // a fast-moving CM frame amplifies float rounding by ~gamma_C^2: this pair's kinematics run in double
+            const double vid[3] = {vi[0], vi[1], vi[2]}, vjd[3] = {vj[0], vj[1], vj[2]};
+            double dd[3];
+            rel_pair_dp<double>(A, ic, vid, vjd, (double)wmax, nmin, f, u23<double>(r.x), u23<double>(r.y),
+                                u23<double>(r.w), dd);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                dvi[d] = (V)(dd[d] / A.ma[ic.a]);
+                dvj[d] = (V)(-dd[d] / A.ma[ic.b]);
+            }
+        } else {
+            if (!(cm.pmag > (V)0)) return;
+            V dp[3];
+            rel_pair_dp_cm<V>(A, ic, cm, cc, wmax, nmin, f, U1, U2, U4, dp);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                dvi[d] = dp[d] / ma;
+                dvj[d] = -dp[d] / mb;
+            }
+        }
+    }
+    bool upd_i = true, upd_j = true;
+    if (!w_equal(t, i, j)) {
+        const bool moves = heavy_moves(t, A, cs, i, j, r.z);
+        if (wi > wj || (wi == wj && w_exact(t, A, cs, i) > w_exact(t, A, cs, j))) upd_i = moves;
+        else upd_j = moves;
+    }
+    if (upd_i) {
+        t.v[i] = vi[0] + dvi[0];
+        t.v[cap + i] = vi[1] + dvi[1];
+        t.v[2 * cap + i] = vi[2] + dvi[2];
+    }
+    if (upd_j) {
+        t.v[j] = vj[0] + dvj[0];
+        t.v[cap + j] = vj[1] + dvj[1];
+        t.v[2 * cap + j] = vj[2] + dvj[2];
+    }
+}
+
+// Energy-correction pairs of fast particles (gamma > 2 for either) run in double on the mixed path: the pair's
+// CM kinetic energy and the Appendix-A quadratic lose ~gamma^2 of float precision for co-moving particles.
+template <class V>
+__device__ __forceinline__ bool fast_pair(V c, const V v1[3], const V v2[3])
+{
+    const V lim = (V)3 * c * c;  // |u|^2 > 3 c^2  <=>  gamma > 2
+    return (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]) > lim || (v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]) > lim;
+}
+
+// Moment correction of one interaction (Sec. 4, Appendix A, Sec. 5.2).
+template <class V, bool REL, int MODE>
+__device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int c, int64_t cs,
+                                    const InterConst& ic, bool intra, int a0, int na, int b0, int nb)
+{
+    const int cap = t.cap;
+    const int nside = intra ? 1 : 2;
+    const V cc = pick<V>(A.c, A.c_f);
+
+    // Eq. vp_pm: per species sums of w (v - v_bs) and w^2 (times m_s later, in FP64)
+    {
+        Acc<V> acc[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = Acc<V>::zero();
+        for (int side = 0; side < nside; ++side) {
+            const int s0 = side ? b0 : a0, ns = side ? nb : na;
+            for (int q = threadIdx.x; q < ns; q += kThreads) {
+                const int i = s0 + q;
+                if constexpr (sizeof(V) == 8) {
+                    const double w = t.w[i];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) acc[side * 4 + d].add(w * (t.v[d * cap + i] - t.vb[d * cap + i]));
+                    acc[side * 4 + 3].add(w * w);
+                } else {
+                    const float2 w = t.w[i];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const ff dd = ff_two_sum(t.v[d * cap + i], -t.vb[d * cap + i]);
+                        acc[side * 4 + d].add(ff_mul({w.x, w.y}, dd));
+                    }
+                    acc[side * 4 + 3].add(ff_mul({w.x, w.y}, {w.x, w.y}));
+                }
+            }
+        }
+        block_sum<V, 8>(acc, sh.red);
+        if (threadIdx.x == 0) {
+            const double* r = sh.red + kWarps * 8;
+            const double ma = A.m[ic.a], mb = A.m[ic.b];
+            const double Sw = ma * r[3] + (intra ? 0.0 : mb * r[7]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double S = ma * r[d] + (intra ? 0.0 : mb * r[4 + d]);
+                sh.B[d] = S / Sw;
+                sh.Bf[d] = (float)sh.B[d];
+            }
+        }
+        __syncthreads();
+        for (int side = 0; side < nside; ++side) {
+            const int s0 = side ? b0 : a0, ns = side ? nb : na;
+            for (int q = threadIdx.x; q < ns; q += kThreads) {
+                const int i = s0 + q;
+                const V w = wv(t, i);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) t.v[d * cap + i] -= pick<V>(sh.B[d], sh.Bf[d]) * w;
+            }
+        }
+        __syncthreads();
+    }
+
+    // Eq. Econs as per-particle energy differences, post-shift species energies and weight sums (Eq. DeltaEs)
+    {
+        Acc<V> acc[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) acc[m] = Acc<V>::zero();
+        for (int side = 0; side < nside; ++side) {
+            const int s0 = side ? b0 : a0, ns = side ? nb : na;
+            for (int q = threadIdx.x; q < ns; q += kThreads) {
+                const int i = s0 + q;
+                const V w = wv(t, i);
+                V dd = 0, v2 = 0, b2 = 0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const V x = t.v[d * cap + i], y = t.vb[d * cap + i];
+                    dd += (x - y) * (x + y);
+                    v2 += x * x;
+                    b2 += y * y;
+                }
+                if (!REL) {
+                    acc[side * 3 + 0].add((V)0.5 * w * dd);
+                    acc[side * 3 + 1].add((V)0.5 * w * v2);
+                } else {
+                    const V c2 = cc * cc;
+                    const V ga = sqrt((V)1 + v2 / c2), gb = sqrt((V)1 + b2 / c2);
+                    acc[side * 3 + 0].add(w * dd / (ga + gb));
+                    acc[side * 3 + 1].add(w * v2 / (ga + (V)1));
+                }
+                if constexpr (sizeof(V) == 8) acc[side * 3 + 2].add(w);
+                else acc[side * 3 + 2].add(ff{t.w[i].x, t.w[i].y});
+            }
+        }
+        block_sum<V, 6>(acc, sh.red);
+        if (threadIdx.x == 0) {
+            const double* r = sh.red + kWarps * 6;
+            const double ma = A.m[ic.a], mb = A.m[ic.b];
+            const double dE = ma * r[0] + (intra ? 0.0 : mb * r[3]);
+            double D0 = dE, D1 = 0.0;
+            int fail = 0;
+            if (!intra) {
+                const bool can0 = na >= 2, can1 = nb >= 2;
+                if (can0 && can1) {
+                    const double wa = r[2] / (double)na * (ma * r[1]);
+                    const double wb = r[5] / (double)nb * (mb * r[4]);
+                    const double den = wa + wb;
+                    if (den > 0.0) {
+                        D0 = wa / den * dE;
+                        D1 = dE - D0;
+                    } else if (dE != 0.0) {
+                        fail = 1;
+                    }
+                } else if (can0) {
+                    D0 = dE;
+                } else if (can1) {
+                    D0 = 0.0;
+                    D1 = dE;
+                } else if (dE != 0.0) {
+                    fail = 1;
+                }
+            }
+            // |Delta E_s| at or below 64 ulps (double) of species s's post-shift kinetic energy counts as zero
+            sh.D[0] = fabs(D0) <= 0x1p-47 * (ma * r[1]) ? 0.0 : D0;
+            sh.D[1] = fabs(D1) <= 0x1p-47 * (intra ? 0.0 : mb * r[4]) ? 0.0 : D1;
+            sh.fail = fail;
+        }
+        __syncthreads();
+    }
+
+    // energy-correction pairs, species a then b
+    int used = 0;
+    for (int side = 0; side < nside; ++side) {
+        if (sh.fail) break;
+        const double D = sh.D[side];
+        if (D == 0.0) continue;
+        const int s0 = side ? b0 : a0, ns = side ? nb : na;
+        const V ms = pick<V>(A.m[side ? ic.b : ic.a], A.m_f[side ? ic.b : ic.a]);
+        const bool sorted = A.sort_by_weight != 0;
+        if (sorted) {
+            for (int q = threadIdx.x; q < ns; q += kThreads)
+                t.keys[s0 + q] = weight_key(w_exact(t, A, cs, t.perm[s0 + q]), (uint32_t)q);
+            __syncthreads();
+            block_sort_u64(t.keys + s0, ns);
+        }
+        auto rho = [&](int m) -> int {
+            return sorted ? t.perm[s0 + (int)(t.keys[s0 + m] & kPermMask)] : t.perm[s0 + m];
+        };
+        V Dabs = (V)fabs(D);
+        const V sgn = D > 0.0 ? (V)1 : (V)-1;
+        const V fE = pick<V>(A.fE, A.fE_f);
+        bool done = false;
+        for (int pass = 0; pass < A.max_corr_passes && !done; ++pass) {
+            const int o = pass & 1;
+            const int np = (ns - o) / 2;
+            V carry = 0;
+            for (int base = 0; base < np && !done; base += kThreads) {
+                const int m = base + threadIdx.x;
+                const bool valid = m < np;
+                int i = 0, j = 0;
+                V v1[3] = {0, 0, 0}, v2[3] = {0, 0, 0}, K = 0, capv = 0, m1 = 1, m2 = 1;
+                if (valid) {
+                    i = rho(o + 2 * m);
+                    j = rho(o + 2 * m + 1);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        v1[d] = t.v[d * cap + i];
+                        v2[d] = t.v[d * cap + j];
+                    }
+                    m1 = ms * wv(t, i);
+                    m2 = ms * wv(t, j);
+                    if (REL && sizeof(V) == 4 && fast_pair(cc, v1, v2)) {
+                        const double d1[3] = {v1[0], v1[1], v1[2]}, d2[3] = {v2[0], v2[1], v2[2]};
+                        K = (V)pair_kecm<double, true>(A.c, A.m[side ? ic.b : ic.a] * w_exact(t, A, cs, i),
+                                                       A.m[side ? ic.b : ic.a] * w_exact(t, A, cs, j), d1, d2);
+                    } else {
+                        K = pair_kecm<V, REL>(cc, m1, m2, v1, v2);
+                    }
+                    capv = K > (V)0 ? fE * K : (V)0;
+                }
+                V total;
+                const V excl = block_exclusive_scan<V>(capv, scan_scratch<V>(sh), total) + carry;
+                if (valid && K > (V)0 && excl < Dabs) {
+                    const V rem = Dabs - excl;
+                    const V U = sgn * (rem < capv ? rem : capv);
+                    if (REL && sizeof(V) == 4 && fast_pair(cc, v1, v2)) {
+                        double d1[3] = {v1[0], v1[1], v1[2]}, d2[3] = {v2[0], v2[1], v2[2]};
+                        const double ms_d = A.m[side ? ic.b : ic.a];
+                        energy_pair<double, true>(A.c, ms_d * w_exact(t, A, cs, i), ms_d * w_exact(t, A, cs, j),
+                                                  (double)K, d1, d2, (double)U);
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            v1[d] = (V)d1[d];
+                            v2[d] = (V)d2[d];
+                        }
+                    } else {
+                        energy_pair<V, REL>(cc, m1, m2, K, v1, v2, U);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        t.v[d * cap + i] = v1[d];
+                        t.v[d * cap + j] = v2[d];
+                    }
+                    ++used;
+                }
+                carry += total;
+                if (carry >= Dabs) done = true;
+            }
+            if (!done) Dabs -= carry;
+        }
+        __syncthreads();
+        if (!done && threadIdx.x == 0) sh.fail = 1;
+        __syncthreads();
+    }
+    const int used_all = block_sum_int(used, sh.iscr);
+    const int failed = sh.fail;
+    if (failed) {
+        if (A.fail_policy == 0) {
+            for (int side = 0; side < nside; ++side) {
+                const int s0 = side ? b0 : a0, ns = side ? nb : na;
+                for (int q = threadIdx.x; q < ns; q += kThreads) {
+                    const int i = s0 + q;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) t.v[d * cap + i] = t.vb[d * cap + i];
+                }
+            }
+        }
+        if (A.fail_policy == 2 && threadIdx.x == 0) latch(A.status, kErrCorrectionFailed);
+    }
+    if (threadIdx.x == 0) {
+        if (MODE == kCorrect) {
+            if (A.corr_pairs) A.corr_pairs[c] = used_all;
+            if (A.fail_count) A.fail_count[c] = failed;
+        } else {
+            if (A.corr_pairs) A.corr_pairs[c] += used_all;
+            if (A.fail_count) A.fail_count[c] += failed;
+        }
+    }
+    __syncthreads();
+}
+
+template <class V, bool REL, int MODE>
+__device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int c, int64_t cs, int k)
+{
+    const InterConst& ic = A.ic[k];
+    const int a = ic.a, b = ic.b;
+    const bool intra = (a == b);
+    const int a0 = sh.off[a], na = sh.off[a + 1] - a0;
+    const int b0 = sh.off[b], nb = sh.off[b + 1] - b0;
+    const uint32_t ictr = (uint32_t)(A.inter_base + k);
+    const int cap = t.cap;
+    const bool active = intra ? (na >= 2) : (na > 0 && nb > 0);
+    if (!active) {
+        if (MODE == kCorrect && threadIdx.x == 0) {
+            if (A.corr_pairs) A.corr_pairs[c] = 0;
+            if (A.fail_count) A.fail_count[c] = 0;
+        }
+        return;
+    }
+    // random permutation of each participating species (counter = {i/2, cell, step, inter<<8 | 1 + side})
+    if (MODE != kScatter) {
+        for (int q = threadIdx.x; q < na; q += kThreads) t.keys[a0 + q] = perm_key(A.rng, c, ictr, 0, q);
+        if (!intra)
+            for (int q = threadIdx.x; q < nb; q += kThreads) t.keys[b0 + q] = perm_key(A.rng, c, ictr, 1, q);
+        __syncthreads();
+        block_sort_u64(t.keys + a0, na);
+        if (!intra) block_sort_u64(t.keys + b0, nb);
+        for (int q = threadIdx.x; q < na; q += kThreads) t.perm[a0 + q] = a0 + (int)(t.keys[a0 + q] & kPermMask);
+        if (!intra)
+            for (int q = threadIdx.x; q < nb; q += kThreads) t.perm[b0 + q] = b0 + (int)(t.keys[b0 + q] & kPermMask);
+        __syncthreads();
+    }
+    const int npairs = intra ? ((na & 1) ? (na + 3) / 2 : na / 2) : (na > nb ? na : nb);
+    const int nmin = intra ? na - 1 : (na < nb ? na : nb);
+    if (MODE == kPair) {
+        for (int p = threadIdx.x; p < npairs; p += kThreads) {
+            int i, j;
+            uint8_t f;
+            pair_at(t, intra, na, nb, a0, b0, p, i, j, f);
+            A.pair_i[cs + p] = (int32_t)(cs + i);
+            A.pair_j[cs + p] = (int32_t)(cs + j);
+            A.pair_flags[cs + p] = f;
+        }
+        __syncthreads();
+        return;
+    }
+    // pre-interaction copy of every participant
+    V* gb = reinterpret_cast<V*>(A.backup);
+    for (int side = 0; side < (intra ? 1 : 2); ++side) {
+        const int s0 = side ? b0 : a0, ns = side ? nb : na;
+        for (int q = threadIdx.x; q < ns; q += kThreads) {
+            const int i = s0 + q;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (MODE == kCorrect) {
+                    t.vb[d * cap + i] = gb[d * A.n_total + cs + i];
+                } else {
+                    const V x = t.v[d * cap + i];
+                    t.vb[d * cap + i] = x;
+                    if (MODE == kScatter) gb[d * A.n_total + cs + i] = x;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (MODE == kFused || MODE == kScatter) {
+        auto get = [&](int p, int& i, int& j, uint8_t& f) {
+            if (MODE == kScatter) {
+                i = (int)(A.pair_i[cs + p] - cs);
+                j = (int)(A.pair_j[cs + p] - cs);
+                f = A.pair_flags[cs + p];
+            } else {
+                pair_at(t, intra, na, nb, a0, b0, p, i, j, f);
+            }
+        };
+        if (intra) {
+            const bool odd = (na & 1) != 0;
+            if (odd && threadIdx.x == 0) {
+                for (int p = 0; p < 3; ++p) {  // the triplet shares particles: in order, one thread
+                    int i, j;
+                    uint8_t f;
+                    get(p, i, j, f);
+                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
+                }
+            }
+            for (int p = (odd ? 3 : 0) + (int)threadIdx.x; p < npairs; p += kThreads) {
+                int i, j;
+                uint8_t f;
+                get(p, i, j, f);
+                scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
+            }
+            __syncthreads();
+        } else {
+            for (int r0 = 0; r0 < npairs; r0 += nmin) {  // rounds of N_min disjoint pairs, in order
+                const int r1 = (r0 + nmin < npairs) ? r0 + nmin : npairs;
+                for (int p = r0 + (int)threadIdx.x; p < r1; p += kThreads) {
+                    int i, j;
+                    uint8_t f;
+                    get(p, i, j, f);
+                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (MODE == kCorrect || (MODE == kFused && A.correct))
+        correct_interaction<V, REL, MODE>(A, t, sh, c, cs, ic, intra, a0, na, b0, nb);
+}
+
+template <class V, bool REL, int MODE>
+__device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Shared& sh)
+{
+    const int S = A.S;
+    const int64_t cs = A.offsets[(int64_t)c * S];
+    const int n = (int)(A.offsets[(int64_t)(c + 1) * S] - cs);
+    Tile<V> t;
+    if (n <= A.cap) {
+        t = make_tile<V>(dyn, A.cap);
+    } else if (A.slab != nullptr && n <= A.slab_cap) {
+        t = make_tile<V>(reinterpret_cast<unsigned char*>(A.slab) + (size_t)blockIdx.x * (size_t)A.slab_stride,
+                         A.slab_cap);
+    } else {
+        if (threadIdx.x == 0) latch(A.status, kErrBounds);
+        return;
+    }
+    if ((int)threadIdx.x <= S) sh.off[threadIdx.x] = (int)(A.offsets[(int64_t)c * S + threadIdx.x] - cs);
+    const int cap = t.cap;
+    V* gx = reinterpret_cast<V*>(A.vx);
+    V* gy = reinterpret_cast<V*>(A.vy);
+    V* gz = reinterpret_cast<V*>(A.vz);
+    if (MODE != kPair) {
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+            t.v[i] = gx[cs + i];
+            t.v[cap + i] = gy[cs + i];
+            t.v[2 * cap + i] = gz[cs + i];
+            w_store(t, i, A.w[cs + i]);
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < A.n_inter; ++k) interaction<V, REL, MODE>(A, t, sh, c, cs, k);
+    if (MODE != kPair) {
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+            gx[cs + i] = t.v[i];
+            gy[cs + i] = t.v[cap + i];
+            gz[cs + i] = t.v[2 * cap + i];
+        }
+    }
+}
+
+template <class V, bool REL, int MODE>
+__global__ void __launch_bounds__(kThreads) cell_kernel(const __grid_constant__ StepArgs A)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ Shared sh;
+    for (;;) {
+        if (threadIdx.x == 0) sh.cell = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int c = sh.cell;
+        if (c >= A.n_cells) break;
+        process_cell<V, REL, MODE>(A, c, dyn, sh);
+        __syncthreads();
+    }
+}
+
+template <class V, bool REL, int MODE>
+const void* kernel_ptr()
+{
+    return reinterpret_cast<const void*>(&cell_kernel<V, REL, MODE>);
+}
+
+const void* select_kernel(bool f32, bool rel, int mode)
+{
+#define MCC_SEL(V, R)                                   \
+    switch (mode) {                                     \
+    case kFused: return kernel_ptr<V, R, kFused>();     \
+    case kPair: return kernel_ptr<V, R, kPair>();       \
+    case kScatter: return kernel_ptr<V, R, kScatter>(); \
+    default: return kernel_ptr<V, R, kCorrect>();       \
+    }
+    if (f32) {
+        if (rel) { MCC_SEL(float, true) }
+        MCC_SEL(float, false)
+    }
+    if (rel) { MCC_SEL(double, true) }
+    MCC_SEL(double, false)
+#undef MCC_SEL
+}
+
+}  // namespace
+
+cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem)
+{
+    return cudaFuncSetAttribute(select_kernel(f32, rel, mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem)
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, select_kernel(f32, rel, mode), kThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st)
+{
+    void* args[] = {const_cast<StepArgs*>(&a)};
+    return cudaLaunchKernel(select_kernel(f32, rel, mode), dim3(grid), dim3(kThreads), args, smem, st);
+}
+
+}  // namespace mcc

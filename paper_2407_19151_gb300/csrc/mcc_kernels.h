@@ -1,0 +1,72 @@
+// Launch interface between the C ABI (mcc_abi.cu) and the kernel translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mcc_device.cuh"
+
+namespace mcc {
+
+enum Mode { kFused = 0, kPair = 1, kScatter = 2, kCorrect = 3 };
+
+// Per-interaction constants, precomputed on the host in FP64 (and rounded once for the mixed path).
+struct InterConst {
+    int32_t a, b;
+    double kappa_mu2;  // q_a^2 q_b^2 lnL_ab dt / (4 pi eps0^2 dV) / mu^2: s = kappa_mu2 w_max N_min / u^3
+    double kappa;      // same without 1/mu^2 (relativistic: s = kappa w_max N_min / (|p*|^2 v_rel*))
+    double mu_ma, mu_mb;
+    float kappa_mu2_f, kappa_f, mu_ma_f, mu_mb_f;
+};
+
+struct StepArgs {
+    const int64_t* offsets;
+    int32_t n_cells, S;
+    int64_t n_total;
+    void* vx;
+    void* vy;
+    void* vz;
+    const double* w;
+    double m[kMaxSpecies];
+    float m_f[kMaxSpecies];
+    double ma[kMaxSpecies];  // species masses for the relativistic kinematics
+    float ma_f[kMaxSpecies];
+    InterConst ic[kMaxInter];
+    int32_t n_inter;
+    int32_t inter_base;  // counter index of ic[0] (unfused calls: the interaction's index in the step)
+    int32_t method, fail_policy, sort_by_weight, max_corr_passes, correct;
+    double c, fE;
+    float c_f, fE_f;
+    RngKey rng;
+    // unfused input / output
+    int32_t* pair_i;
+    int32_t* pair_j;
+    uint8_t* pair_flags;
+    void* backup;
+    int32_t* corr_pairs;
+    int32_t* fail_count;
+    int32_t accumulate;
+    // control
+    int32_t* status;
+    int32_t* queue;
+    int32_t cap;        // particles per cell staged in shared memory
+    char* slab;         // per-CTA global slabs for larger cells (may be null)
+    int64_t slab_stride;
+    int32_t slab_cap;
+};
+
+// Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation).
+inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4; }
+
+// Kernel launches (defined in mcc_cell.cu / mcc_bin.cu).
+cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
+int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem);
+cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem);
+
+cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
+                       int32_t* perm, int64_t* offsets, void* ws, int32_t* status, cudaStream_t st, int64_t* launches);
+size_t bin_workspace_bytes(int64_t n, int64_t n_keys);
+cudaError_t launch_gather(const void* in, const int32_t* perm, int64_t n, int elem_bytes, void* out, cudaStream_t st);
+
+}  // namespace mcc

