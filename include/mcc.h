@@ -181,8 +181,9 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* 
                    int32_t n_inter, const mcc_params* params, int32_t n_steps, int32_t max_cell,
                    int32_t* corr_pairs, int32_t* fail_count, void* ws, size_t ws_bytes, mcc_stream stream);
 
-/* Particles staged on chip per cell by mcc_step_fused (0 = automatic: min(largest cell, 2048, what fits in
- * shared memory)). Cells above it run from the workspace slabs. Used by the autotuner. */
+/* Particles staged on chip per cell by mcc_step_fused (0 = automatic: the largest tile with which four CTAs share
+ * an SM's shared memory, or the largest cell if smaller). Cells above it run from the workspace slabs. Used by the
+ * autotuner. */
 int mcc_set_tile_cap(mcc_ctx* ctx, int32_t cap);
 
 /* Synchronise `stream`, read and clear the device status word; returns MCC_OK or the first latched error. */

@@ -74,7 +74,7 @@ def lib():
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.lib_path()
+    path = os.environ.get("MCC_LIBRARY") or _build.lib_path()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built ({path}); run paper_2407_19151_gb300.build()")
     L = C.CDLL(path)

@@ -15,6 +15,7 @@ HEADERS = ["mcc_device.cuh", "mcc_kernels.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+EXTRA = os.environ.get("MCC_NVCC_FLAGS", "").split()
 
 
 def lib_path() -> str:
@@ -26,17 +27,16 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, out: str | None = None) -> str:
     """Compile every translation unit in parallel, link the shared library; skip if up to date."""
-    out = lib_path()
+    out = out or lib_path()
     if not force and os.path.exists(out) and os.path.getmtime(out) >= _newest_input():
         return out
-    os.makedirs(BUILD, exist_ok=True)
-    tag = platform.machine()
+    os.makedirs(os.path.dirname(out), exist_ok=True)
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, f"{os.path.splitext(src)[0]}.{tag}.o")
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(os.path.dirname(out), f"{os.path.splitext(src)[0]}.{os.path.basename(out)}.o")
+        cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -13,6 +13,7 @@ struct mcc_ctx {
     int64_t launches;
     int num_sms;
     size_t smem_optin;
+    size_t smem_per_sm;
     int32_t tile_cap;  // particles staged on chip per cell; 0 = automatic
 };
 
@@ -20,8 +21,8 @@ namespace {
 
 using mcc::StepArgs;
 
-constexpr size_t kStaticSmemReserve = 2048;  // Shared struct of the cell kernel plus margin
-constexpr int kAutoTileCap = 2048;           // default on-chip tile when cells are larger
+constexpr size_t kStaticSmemReserve = 1024;  // margin above the cell kernel's static shared memory
+constexpr int kAutoCtasPerSm = 4;             // automatic tile: this many CTAs share one SM's shared memory
 constexpr int kMaxCtasPerSm = 2048 / mcc::kThreads;
 
 cudaStream_t S(mcc_stream s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -120,10 +121,22 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
     return MCC_OK;
 }
 
+// Largest on-chip tile (particles) one CTA can stage: the opt-in shared memory minus the kernel's static part.
 size_t max_tile_particles(const mcc_ctx* ctx, bool f32)
 {
-    const size_t avail = ctx->smem_optin > kStaticSmemReserve ? ctx->smem_optin - kStaticSmemReserve : 0;
+    const size_t fixed = mcc::cell_kernel_static_smem(f32, true, mcc::kFused) + kStaticSmemReserve;
+    const size_t avail = ctx->smem_optin > fixed ? ctx->smem_optin - fixed : 0;
     return avail / mcc::tile_bytes_per_particle(f32);
+}
+
+// Automatic tile: the largest that still lets kAutoCtasPerSm CTAs share an SM's shared memory.
+int auto_tile(const mcc_ctx* ctx, bool f32)
+{
+    const size_t fixed = mcc::cell_kernel_static_smem(f32, true, mcc::kFused) + 1024;
+    const size_t per_cta = ctx->smem_per_sm / kAutoCtasPerSm;
+    const size_t t = per_cta > fixed ? (per_cta - fixed) / mcc::tile_bytes_per_particle(f32) : 64;
+    const size_t capmax = max_tile_particles(ctx, f32);
+    return (int)(t < capmax ? t : capmax);
 }
 
 // Launch one cell-kernel pass over every cell (queue reset, persistent grid of at most max_grid CTAs).
@@ -161,8 +174,10 @@ int mcc_create(mcc_ctx** out, int device)
     c->device = device;
     c->launches = 0;
     c->tile_cap = 0;
-    int optin = 0, sms = 0;
+    int optin = 0, sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    c->smem_per_sm = (size_t)per_sm;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     c->smem_optin = (size_t)optin;
     c->num_sms = sms;
@@ -281,7 +296,7 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t max_cell, size_t
     const bool f32 = prec == MCC_F32_MIXED;
     const size_t capmax = max_tile_particles(ctx, f32);
     const int tile = ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
-                                       : (int)((size_t)kAutoTileCap < capmax ? (size_t)kAutoTileCap : capmax);
+                                       : auto_tile(ctx, f32);
     if (max_cell <= tile) {
         *bytes = 0;
         return MCC_OK;
@@ -311,7 +326,7 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
     const bool rel = p->relativistic != 0;
     const size_t capmax = max_tile_particles(ctx, f32);
     const int tile = ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
-                                       : (int)((size_t)kAutoTileCap < capmax ? (size_t)kAutoTileCap : capmax);
+                                       : auto_tile(ctx, f32);
     const int cap = max_cell <= tile ? (max_cell > 0 ? max_cell : 1) : tile;
     int max_grid = 1 << 30;
     if (max_cell > tile) {

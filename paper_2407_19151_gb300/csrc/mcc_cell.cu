@@ -17,6 +17,10 @@
 // per-cell sums, FP64 only for the per-cell coefficients (B, Delta E, its split) computed by one thread.
 #include "mcc_kernels.h"
 
+#ifndef MCC_MIN_BLOCKS
+#define MCC_MIN_BLOCKS 4
+#endif
+
 namespace mcc {
 namespace {
 
@@ -33,11 +37,12 @@ struct WStore<float> {
 
 template <class V>
 struct Tile {
-    uint64_t* keys;
+    uint64_t* keys;  // sort keys of segments too large for one warp's registers
     typename WStore<V>::T* w;
-    V* v;   // [3][cap]
-    V* vb;  // [3][cap] pre-interaction copy
-    int32_t* perm;
+    V* v;            // [3][cap]
+    V* vb;           // [3][cap] pre-interaction copy
+    int32_t* perm;   // random permutation of each species segment (cell-local indices)
+    int32_t* rho;    // weight-descending order of each species segment (cell-local indices)
     int cap;
 };
 
@@ -51,6 +56,7 @@ __device__ __forceinline__ Tile<V> make_tile(unsigned char* base, int cap)
     t.v = reinterpret_cast<V*>(base + 16 * (size_t)cap);
     t.vb = t.v + 3 * (size_t)cap;
     t.perm = reinterpret_cast<int32_t*>(base + (16 + 6 * sizeof(V)) * (size_t)cap);
+    t.rho = t.perm + cap;
     return t;
 }
 
@@ -78,16 +84,133 @@ __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 struct Shared {
     int off[kMaxSpecies + 1];
+    int wmode[kMaxSpecies];  // weight order: 0 distinct (rho fixed for the visit), 1 all equal (rho = perm), 2 ties
     int cell;
     int fail;
-    double red[kWarps * 8 + 8];
+    alignas(16) unsigned char red_raw[8 * kThreads * 8];  // block_sum partials (8 quantities x 8 bytes)
+    double red[8];
     double scan_d[kWarps + 1];
     float scan_f[kWarps + 1];
+    int iscan[kWarps + 1];
     int iscr[kWarps];
     double B[3];
     float Bf[3];
     double D[2];
 };
+
+constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp in registers
+
+// Ascending sort of n <= 512 keys in buf (shared or global) by the calling warp: loaded K per lane into registers,
+// bitonic network, stored back. One out-of-line copy per K keeps register pressure and code size off the callers.
+template <int K>
+__device__ __noinline__ void warp_sort_buf_k(uint64_t* buf, int n)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t x[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        x[r] = pos < n ? buf[pos] : ~0ull;
+    }
+    warp_bitonic<K>(x);
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        if (pos < n) buf[pos] = x[r];
+    }
+}
+
+__device__ __forceinline__ void warp_sort_buf(uint64_t* buf, int n)
+{
+    __syncwarp();
+    if (n <= 32) warp_sort_buf_k<1>(buf, n);
+    else if (n <= 64) warp_sort_buf_k<2>(buf, n);
+    else if (n <= 128) warp_sort_buf_k<4>(buf, n);
+    else if (n <= 256) warp_sort_buf_k<8>(buf, n);
+    else warp_sort_buf_k<16>(buf, n);
+    __syncwarp();
+}
+
+// Random permutations of the interaction's one or two species segments: local indices ordered by their 64-bit
+// Philox keys (44 random bits above the index). The random bits are uniform, so a counting sort on their top
+// log2(B) bits (B = next power of two >= n buckets) already places almost every key; each bucket holding several
+// keys is finished by an insertion sort on the full key. The result is the sort by full key (keys are distinct).
+// Scratch: the pre-interaction copy vb (unused until after the permutations) holds the bucket counters.
+template <class V>
+__device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, int c, uint32_t ictr, int nside,
+                             int a0, int na, int b0, int nb)
+{
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(t.vb);
+    const int s0v[2] = {a0, b0}, nv[2] = {na, nb};
+    int lgB[2] = {0, 0}, Bv[2] = {0, 0};
+    for (int side = 0; side < nside; ++side) {
+        while ((1 << lgB[side]) < nv[side]) ++lgB[side];
+        Bv[side] = 1 << lgB[side];
+    }
+    const int base1 = Bv[0];
+    const int L = Bv[0] + (nside > 1 ? Bv[1] : 0);
+    for (int side = 0; side < nside; ++side)
+        for (int q = threadIdx.x; q < nv[side]; q += kThreads)
+            t.keys[s0v[side] + q] = perm_key(A.rng, c, ictr, side, q);
+    for (int b = threadIdx.x; b < L; b += kThreads) cnt[b] = 0;
+    __syncthreads();
+    for (int side = 0; side < nside; ++side) {
+        const int base = side ? base1 : 0;
+        for (int q = threadIdx.x; q < nv[side]; q += kThreads) {
+            const uint64_t k = t.keys[s0v[side] + q];
+            const int b = lgB[side] ? (int)(k >> (64 - lgB[side])) : 0;
+            atomicAdd(&cnt[base + b], 1u);
+        }
+    }
+    __syncthreads();
+    // exclusive scan over both sides' buckets (side 1's positions are offset by na)
+    {
+        const int chunk = (L + kThreads - 1) / kThreads;
+        const int lo = threadIdx.x * chunk, hi = min(L, lo + chunk);
+        int local = 0;
+        for (int b = lo; b < hi; ++b) local += (int)cnt[b];
+        int total;
+        int run = block_exclusive_scan<int>(local, sh.iscan, total);
+        for (int b = lo; b < hi; ++b) {
+            const int x = (int)cnt[b];
+            cnt[b] = (uint32_t)run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    for (int side = 0; side < nside; ++side) {
+        const int base = side ? base1 : 0, off = side ? na : 0;
+        for (int q = threadIdx.x; q < nv[side]; q += kThreads) {
+            const uint64_t k = t.keys[s0v[side] + q];
+            const int b = lgB[side] ? (int)(k >> (64 - lgB[side])) : 0;
+            const int pos = (int)atomicAdd(&cnt[base + b], 1u) - off;
+            t.perm[s0v[side] + pos] = q;
+        }
+    }
+    __syncthreads();
+    // cnt[b] now holds the end of bucket b: finish buckets with several keys, then store cell-local indices
+    for (int side = 0; side < nside; ++side) {
+        const int base = side ? base1 : 0, off = side ? na : 0, s0 = s0v[side];
+        for (int b = threadIdx.x; b < Bv[side]; b += kThreads) {
+            const int end = (int)cnt[base + b] - off;
+            const int start = b ? (int)cnt[base + b - 1] - off : 0;
+            for (int x = start + 1; x < end; ++x) {
+                const int v = t.perm[s0 + x];
+                const uint64_t kv = t.keys[s0 + v];
+                int y = x - 1;
+                while (y >= start && t.keys[s0 + t.perm[s0 + y]] > kv) {
+                    t.perm[s0 + y + 1] = t.perm[s0 + y];
+                    --y;
+                }
+                t.perm[s0 + y + 1] = v;
+            }
+        }
+    }
+    __syncthreads();
+    for (int side = 0; side < nside; ++side)
+        for (int q = threadIdx.x; q < nv[side]; q += kThreads) t.perm[s0v[side] + q] += s0v[side];
+    __syncthreads();
+}
 
 template <class V>
 __device__ __forceinline__ V* scan_scratch(Shared& sh);
@@ -304,9 +427,9 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 }
             }
         }
-        block_sum<V, 8>(acc, sh.red);
+        block_sum<V, 8>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
         if (threadIdx.x == 0) {
-            const double* r = sh.red + kWarps * 8;
+            const double* r = sh.red;
             const double ma = A.m[ic.a], mb = A.m[ic.b];
             const double Sw = ma * r[3] + (intra ? 0.0 : mb * r[7]);
 #pragma unroll
@@ -360,9 +483,9 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 else acc[side * 3 + 2].add(ff{t.w[i].x, t.w[i].y});
             }
         }
-        block_sum<V, 6>(acc, sh.red);
+        block_sum<V, 6>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
         if (threadIdx.x == 0) {
-            const double* r = sh.red + kWarps * 6;
+            const double* r = sh.red;
             const double ma = A.m[ic.a], mb = A.m[ic.b];
             const double dE = ma * r[0] + (intra ? 0.0 : mb * r[3]);
             double D0 = dE, D1 = 0.0;
@@ -403,17 +526,34 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
         const double D = sh.D[side];
         if (D == 0.0) continue;
         const int s0 = side ? b0 : a0, ns = side ? nb : na;
-        const V ms = pick<V>(A.m[side ? ic.b : ic.a], A.m_f[side ? ic.b : ic.a]);
-        const bool sorted = A.sort_by_weight != 0;
-        if (sorted) {
-            for (int q = threadIdx.x; q < ns; q += kThreads)
-                t.keys[s0 + q] = weight_key(w_exact(t, A, cs, t.perm[s0 + q]), (uint32_t)q);
-            __syncthreads();
-            block_sort_u64(t.keys + s0, ns);
+        const int spc = side ? ic.b : ic.a;
+        const V ms = pick<V>(A.m[spc], A.m_f[spc]);
+        // order of the energy pairs: the random permutation, stably sorted by descending weight (optional step of
+        // Algorithm 1). Distinct weights: the order fixed at the cell's load; all equal: the permutation itself;
+        // partial ties: sorted here by (weight, rank in the permutation).
+        const int mode = A.sort_by_weight ? sh.wmode[spc] : 1;
+        if (mode == 2) {
+            if (ns <= kWarpSortMax) {
+                if (threadIdx.x < 32) {
+                    for (int r = threadIdx.x; r < ns; r += 32)
+                        t.keys[s0 + r] = weight_key(w_exact(t, A, cs, t.perm[s0 + r]), (uint32_t)r);
+                    warp_sort_buf(t.keys + s0, ns);
+                    for (int m = threadIdx.x; m < ns; m += 32)
+                        t.rho[s0 + m] = t.perm[s0 + (int)(t.keys[s0 + m] & kPermMask)];
+                }
+                __syncthreads();
+            } else {
+                for (int q = threadIdx.x; q < ns; q += kThreads)
+                    t.keys[s0 + q] = weight_key(w_exact(t, A, cs, t.perm[s0 + q]), (uint32_t)q);
+                __syncthreads();
+                block_sort_u64(t.keys + s0, ns);
+                for (int q = threadIdx.x; q < ns; q += kThreads)
+                    t.rho[s0 + q] = t.perm[s0 + (int)(t.keys[s0 + q] & kPermMask)];
+                __syncthreads();
+            }
         }
-        auto rho = [&](int m) -> int {
-            return sorted ? t.perm[s0 + (int)(t.keys[s0 + m] & kPermMask)] : t.perm[s0 + m];
-        };
+        const int32_t* order = (mode == 1) ? t.perm : t.rho;
+        auto rho = [&](int m) -> int { return order[s0 + m]; };
         V Dabs = (V)fabs(D);
         const V sgn = D > 0.0 ? (V)1 : (V)-1;
         const V fE = pick<V>(A.fE, A.fE_f);
@@ -526,18 +666,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
         return;
     }
     // random permutation of each participating species (counter = {i/2, cell, step, inter<<8 | 1 + side})
-    if (MODE != kScatter) {
-        for (int q = threadIdx.x; q < na; q += kThreads) t.keys[a0 + q] = perm_key(A.rng, c, ictr, 0, q);
-        if (!intra)
-            for (int q = threadIdx.x; q < nb; q += kThreads) t.keys[b0 + q] = perm_key(A.rng, c, ictr, 1, q);
-        __syncthreads();
-        block_sort_u64(t.keys + a0, na);
-        if (!intra) block_sort_u64(t.keys + b0, nb);
-        for (int q = threadIdx.x; q < na; q += kThreads) t.perm[a0 + q] = a0 + (int)(t.keys[a0 + q] & kPermMask);
-        if (!intra)
-            for (int q = threadIdx.x; q < nb; q += kThreads) t.perm[b0 + q] = b0 + (int)(t.keys[b0 + q] & kPermMask);
-        __syncthreads();
-    }
+    if (MODE != kScatter) permutations<V>(A, t, sh, c, ictr, intra ? 1 : 2, a0, na, b0, nb);
     const int npairs = intra ? ((na & 1) ? (na + 3) / 2 : na / 2) : (na > nb ? na : nb);
     const int nmin = intra ? na - 1 : (na < nb ? na : nb);
     if (MODE == kPair) {
@@ -645,6 +774,31 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
         }
     }
     __syncthreads();
+    // weight-descending order of each species, fixed for this visit when the (truncated) weights are distinct
+    if ((MODE == kFused || MODE == kCorrect) && A.sort_by_weight) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int sp = 0; sp < S; ++sp) {
+            const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
+            if (ns > kWarpSortMax) {
+                if (threadIdx.x == 0) sh.wmode[sp] = 2;
+                continue;
+            }
+            if (warp != sp % kWarps) continue;
+            if (ns < 2) {
+                if (lane == 0) sh.wmode[sp] = 0;
+                continue;
+            }
+            int tie = 0;
+            for (int q = lane; q < ns; q += 32) t.keys[s0 + q] = weight_key(w_exact(t, A, cs, s0 + q), (uint32_t)q);
+            warp_sort_buf(t.keys + s0, ns);
+            for (int q = lane; q < ns; q += 32) t.rho[s0 + q] = s0 + (int)(t.keys[s0 + q] & kPermMask);
+            for (int q = lane; q + 1 < ns; q += 32) tie |= (t.keys[s0 + q] >> kPermBits) == (t.keys[s0 + q + 1] >> kPermBits);
+            tie = __any_sync(0xffffffffu, tie);
+            const bool all_equal = (t.keys[s0] >> kPermBits) == (t.keys[s0 + ns - 1] >> kPermBits);
+            if (lane == 0) sh.wmode[sp] = all_equal ? 1 : (tie ? 2 : 0);
+        }
+        __syncthreads();
+    }
     for (int k = 0; k < A.n_inter; ++k) interaction<V, REL, MODE>(A, t, sh, c, cs, k);
     if (MODE != kPair) {
         for (int i = threadIdx.x; i < n; i += kThreads) {
@@ -656,7 +810,7 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
 }
 
 template <class V, bool REL, int MODE>
-__global__ void __launch_bounds__(kThreads) cell_kernel(const __grid_constant__ StepArgs A)
+__global__ void __launch_bounds__(kThreads, MCC_MIN_BLOCKS) cell_kernel(const __grid_constant__ StepArgs A)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ Shared sh;
@@ -695,6 +849,13 @@ const void* select_kernel(bool f32, bool rel, int mode)
 }
 
 }  // namespace
+
+size_t cell_kernel_static_smem(bool f32, bool rel, int mode)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, select_kernel(f32, rel, mode)) != cudaSuccess) return 16384;
+    return fa.sharedSizeBytes;
+}
 
 cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem)
 {

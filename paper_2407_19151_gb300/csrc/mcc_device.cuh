@@ -9,7 +9,10 @@
 
 namespace mcc {
 
-constexpr int kThreads = 256;
+#ifndef MCC_THREADS
+#define MCC_THREADS 128
+#endif
+constexpr int kThreads = MCC_THREADS;  // threads cooperating on one cell (one CTA)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxInter = kMaxSpecies * (kMaxSpecies + 1) / 2;
@@ -195,28 +198,24 @@ struct Acc<float> {
     }
 };
 
-// Block-wide sum of M accumulators (fixed tree order, so the result is reproducible). The M sums are left in
-// scratch[kWarps * M + m] for the caller (typically thread 0) to read before the next barrier-separated use.
-// scratch: shared, at least kWarps * M + M doubles. Must be called by all threads of the block.
+// Block-wide sum of M accumulators in a fixed order (reproducible). Each thread parks its M partial sums in shared
+// memory; warp w then reduces quantities w, w + kWarps, ... (its lanes add kThreads/32 partials each, then a warp
+// tree). The M sums are left in out[m] (shared) for the caller to read after the final barrier.
+// scratch: shared, M * kThreads * sizeof(Acc<V>) bytes. Must be called by all threads of the block.
 template <class V, int M>
-__device__ __forceinline__ void block_sum(Acc<V> (&a)[M], double* scratch)
+__device__ __forceinline__ void block_sum(Acc<V> (&a)[M], Acc<V>* scratch, double* out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a[m].add(a[m].shfl_xor(o));
-    }
-    // warp partials are combined in double: kWarps values per quantity, a few DADD per block
-    if (lane == 0) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) scratch[warp * M + m] = a[m].value();
-    }
+    for (int m = 0; m < M; ++m) scratch[m * kThreads + threadIdx.x] = a[m];
     __syncthreads();
-    if (threadIdx.x < M) {
-        double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += scratch[w * M + threadIdx.x];
-        scratch[kWarps * M + threadIdx.x] = s;
+    for (int m = warp; m < M; m += kWarps) {
+        Acc<V> s = scratch[m * kThreads + lane];
+#pragma unroll
+        for (int k = 1; k < kThreads / 32; ++k) s.add(scratch[m * kThreads + lane + 32 * k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s.add(s.shfl_xor(o));
+        if (lane == 0) out[m] = s.value();
     }
     __syncthreads();
 }
@@ -268,6 +267,48 @@ __device__ __forceinline__ int block_sum_int(int x, int* scratch)
     for (int w = 0; w < kWarps; ++w) s += scratch[w];
     __syncthreads();
     return s;
+}
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
+{
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Bitonic sort (ascending) of 32*K 64-bit keys held in registers by one warp, K per lane: lane l holds positions
+// l*K .. l*K + K - 1. Strides below K stay in the lane's registers, larger ones exchange with lane ^ (stride / K).
+template <int K>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&x)[K])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32 * K; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= K) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int pos = lane * K + r;
+                    const uint64_t y = shfl_xor_u64(x[r], stride / K);
+                    const bool keep_min = ((pos & size) == 0) == ((pos & stride) == 0);
+                    x[r] = keep_min ? (x[r] < y ? x[r] : y) : (x[r] < y ? y : x[r]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    if ((r & stride) == 0) {
+                        const int pos = lane * K + r;
+                        const uint64_t a = x[r], b = x[r + stride];
+                        const bool up = (pos & size) == 0;
+                        const bool swap = up ? (a > b) : (a < b);
+                        x[r] = swap ? b : a;
+                        x[r + stride] = swap ? a : b;
+                    }
+                }
+            }
+        }
+    }
 }
 
 // Ascending sort of n 64-bit keys in place (shared or global memory), block-wide. Bitonic network in its "flip"
@@ -403,8 +444,10 @@ __device__ __forceinline__ V n97_A(V s)
         const V t = (V)3 * ((V)1 - z);       // L(A) ~ A/3 - A^3/45 inverted to second order
         A = t * ((V)1 + t * t / (V)15);
     }
-    const int iters = sizeof(V) == 8 ? 40 : 12;
-    const V tol = sizeof(V) == 8 ? (V)2e-16 : (V)1e-7;
+    // Newton converges quadratically: once a step is a few ulps the next would only chase rounding noise in G, so
+    // stop there (a step of 4 ulps leaves an error far below one ulp).
+    const int iters = sizeof(V) == 8 ? 24 : 10;
+    const V tol = sizeof(V) == 8 ? (V)1e-15 : (V)5e-7;
     for (int it = 0; it < iters; ++it) {
         V G, dG;
         n97_G_dG(A, G, dG);

@@ -56,13 +56,14 @@ struct StepArgs {
     int32_t slab_cap;
 };
 
-// Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation).
-inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4; }
+// Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation, weight order).
+inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
 
 // Kernel launches (defined in mcc_cell.cu / mcc_bin.cu).
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
 int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem);
 cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem);
+size_t cell_kernel_static_smem(bool f32, bool rel, int mode);
 
 cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
                        int32_t* perm, int64_t* offsets, void* ws, int32_t* status, cudaStream_t st, int64_t* launches);

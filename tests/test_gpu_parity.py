@@ -146,7 +146,15 @@ FUSED_F64 = [
     ("momentum_only", lambda: W.relativistic_beam(n_cells=40, count_lo=4, count_hi=40, precision="f64"),
      {"fail_policy": 1, "dt_scale": 20}),
     ("relativistic", lambda: W.relativistic_beam(n_cells=40, count_lo=16, count_hi=300, precision="f64"), {}),
+    ("tied_weights", lambda: _tied(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
+    ("large_segments", lambda: W.differentiable(n_cells=4, per_species=1500), {}),
 ]
+
+
+def _tied(wl):
+    """Weights from a three-value set: ties inside every species exercise the per-interaction weight sort."""
+    wl.w[:] = np.random.default_rng(5).choice([1.0, 2.0, 40.0], size=wl.n)
+    return wl
 
 
 def _run_fused(mcc, wl, dtype, n_steps=2, **kw):
