@@ -109,6 +109,26 @@ int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n
             int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws, size_t ws_bytes,
             mcc_stream stream);
 
+/*
+ * mcc_bin_static: the same cell sort as mcc_bin for callers that cannot allocate device memory at all, such as
+ * code running under an allocator that must not grow, inside a host callback or driver-level integration where
+ * cudaMalloc is unavailable, or a caller without a context to own a workspace. It takes no context and no
+ * workspace: its counters live in one file-scope device array of MCC_BIN_STATIC_MAX_KEYS segment counters (two
+ * int32 arrays, about 16 MiB) that every GPU loading this library holds until the process exits. The paper has no
+ * counterpart; this is an allocation-free variant of mcc_bin.
+ *   Arguments and outputs as mcc_bin; n_cells * n_species above MCC_BIN_STATIC_MAX_KEYS returns MCC_ERR_TOO_LARGE
+ *   before any work is enqueued. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   The first call on a device looks up that device's address of the array (cudaGetSymbolAddress, with the device
+ *   current), so make the first call on each device before any stream capture.
+ *   Every call clears the counters it uses on its stream before use, but all calls share the one array: calls that
+ *   overlap on the GPU (different streams, or a second call before the first finished) race.
+ *   There is no status word: particles with out-of-range cell or species are dropped, which shows as
+ *   offsets_out[last] < n.
+ */
+#define MCC_BIN_STATIC_MAX_KEYS (1 << 21)
+int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
+                   int32_t* perm_out, int64_t* offsets_out, mcc_stream stream);
+
 /* Gather a double or float array through perm: out[k] = in[perm[k]] (elem_bytes 4 or 8). */
 int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream);
 

@@ -85,6 +85,7 @@ def lib():
         "mcc_bin_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_bin": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
         "mcc_gather": (C.c_int, [vp, vp, C.c_int64, C.c_int32, vp, vp]),
+        "mcc_bin_static": (C.c_int, [vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp]),
         "mcc_pair": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                C.c_uint64, vp, vp, vp, vp]),
         "mcc_scatter": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), P(C.c_double),
@@ -212,6 +213,20 @@ def mcc_bin(cell: torch.Tensor, species: torch.Tensor, n_cells: int, n_species: 
     ws = ctx.workspace("bin", nb.value)
     _check(lib().mcc_bin(ctx.handle, _ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
                          _ptr(ws), nb.value, _stream(stream, cell.device)), "mcc_bin")
+    return perm, offsets
+
+
+def mcc_bin_static(cell: torch.Tensor, species: torch.Tensor, n_cells: int, n_species: int, perm=None,
+                   offsets=None, stream=None):
+    """Allocation-free cell sort (library-held counters, no context, no workspace); outputs as mcc_bin. The output
+    tensors may be passed in, so that the call itself allocates nothing."""
+    n = cell.numel()
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=cell.device)
+    if offsets is None:
+        offsets = torch.empty(n_cells * n_species + 1, dtype=torch.int64, device=cell.device)
+    _check(lib().mcc_bin_static(_ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
+                                _stream(stream, cell.device)), "mcc_bin_static")
     return perm, offsets
 
 

@@ -216,6 +216,16 @@ int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n
                                        S(stream), &ctx->launches));
 }
 
+int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
+                   int32_t* perm_out, int64_t* offsets_out, mcc_stream stream)
+{
+    if (n < 0 || n_cells <= 0 || n_species <= 0 || !offsets_out) return MCC_ERR_INVALID_ARG;
+    if (n > 0 && (!cell || !species || !perm_out)) return MCC_ERR_INVALID_ARG;
+    if (n > INT32_MAX || (int64_t)n_cells * n_species > mcc::static_bin_max_keys()) return MCC_ERR_TOO_LARGE;
+    return cuda_status(mcc::launch_bin_static(cell, species, n, n_cells, n_species, perm_out, offsets_out,
+                                              S(stream)));
+}
+
 int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream)
 {
     if (n < 0 || (elem_bytes != 4 && elem_bytes != 8) || (n > 0 && (!in || !perm || !out))) return MCC_ERR_INVALID_ARG;

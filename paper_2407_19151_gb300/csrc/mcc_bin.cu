@@ -4,7 +4,15 @@
 // histogram (atomic counts) -> exclusive scan -> scatter with atomic cursors (order within a segment arbitrary)
 // -> per-segment sort of the particle indices, which restores the stable (index) order. The result does not depend
 // on the order in which the atomics were served.
+#include <mutex>
+
 #include "mcc_kernels.h"
+
+// Counters of mcc_bin_static: every device that loads the library holds this array until the process exits.
+// counts | cursors, each 4 * kStaticBinKeys bytes rounded to 256 (the layout launch_bin expects).
+constexpr int64_t kStaticBinKeys = 1 << 21;
+constexpr size_t kStaticBinHalf = ((size_t)kStaticBinKeys * sizeof(int32_t) + 255) & ~(size_t)255;
+static __device__ __align__(256) int32_t g_bin_static_scratch[2 * kStaticBinHalf / sizeof(int32_t)];
 
 namespace mcc {
 namespace {
@@ -135,6 +143,44 @@ cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, i
     }
     *launches += 1;
     return cudaGetLastError();
+}
+
+// Device address of g_bin_static_scratch on the current device. The host-side name is only a stand-in, so the
+// address is looked up once per device (with that device current) and cached.
+static void* static_bin_scratch(int* err)
+{
+    static std::mutex mu;
+    static void* addr[256] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        *err = 1;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bin_static_scratch) != cudaSuccess || !p) {
+            *err = 1;
+            return nullptr;
+        }
+        addr[dev] = p;
+    }
+    *err = 0;
+    return addr[dev];
+}
+
+int64_t static_bin_max_keys() { return kStaticBinKeys; }
+
+cudaError_t launch_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
+                              int32_t n_species, int32_t* perm, int64_t* offsets, cudaStream_t st)
+{
+    int err = 0;
+    void* ws = static_bin_scratch(&err);
+    if (err) return cudaErrorInvalidSymbol;
+    int64_t launches = 0;
+    // launch_bin clears both counter arrays on the stream before its kernels; no status word (out-of-range
+    // particles are dropped, visible as offsets[last] < n)
+    return launch_bin(cell, species, n, n_cells, n_species, perm, offsets, ws, nullptr, st, &launches);
 }
 
 cudaError_t launch_gather(const void* in, const int32_t* perm, int64_t n, int elem_bytes, void* out, cudaStream_t st)
