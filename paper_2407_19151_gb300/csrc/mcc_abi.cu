@@ -9,7 +9,7 @@
 
 struct mcc_ctx {
     int device;
-    int32_t* dbuf;  // [0] status word, [1] work-queue counter
+    int32_t* dbuf;  // [0] status word, [1] work-queue counter, then the N97 tables
     int64_t launches;
     int num_sms;
     size_t smem_optin;
@@ -17,12 +17,83 @@ struct mcc_ctx {
     int32_t tile_cap;  // particles staged on chip per cell; 0 = automatic
 };
 
+namespace mcc {
+
+// N97 table on the host, in double: A(s) solves G(A) = 1 - coth A + 1/A = 1 - e^-s (bisection to the last bit);
+// stored as f = ln(A s) and h df/dx at x = ln s, where df/dx = 1 + s e^-s / (A G'(A)) by implicit
+// differentiation, G'(A) = -(1/A^2 - 1/sinh^2 A).
+namespace {
+void laurent(double A, double& L, double& dL)
+{
+    // coth A - 1/A = sum_n 2^{2n} B_{2n} A^{2n-1} / (2n)!, for A < 1/2
+    static const double c[12] = {1.0 / 3.0,       -1.0 / 45.0,        2.0 / 945.0,        -1.0 / 4725.0,
+                                 2.0 / 93555.0,   -1382.0 / 638512875.0, 4.0 / 18243225.0, -3617.0 / 162820783125.0,
+                                 87734.0 / 38979295480125.0, -349222.0 / 1531329465290625.0,
+                                 310732.0 / 13447856940643125.0, -472728182.0 / 201919571963756521875.0};
+    L = 0.0;
+    dL = 0.0;
+    double p = A;
+    for (int n = 0; n < 12; ++n) {
+        L += c[n] * p;
+        dL += (2 * n + 1) * c[n] * (p / A);
+        p *= A * A;
+    }
+}
+double G_of(double A)
+{
+    if (A < 0.5) {
+        double L, dL;
+        laurent(A, L, dL);
+        return 1.0 - L;
+    }
+    return 1.0 / A - 2.0 / std::expm1(2.0 * A);
+}
+double dG_of(double A)
+{
+    if (A < 0.5) {
+        double L, dL;
+        laurent(A, L, dL);
+        return -dL;
+    }
+    const double sh = std::sinh(A);
+    return -(1.0 / (A * A) - (A < 350.0 ? 1.0 / (sh * sh) : 0.0));
+}
+}  // namespace
+
+void n97_table(double* f, double* dh)
+{
+    for (int k = 0; k <= kN97Nodes; ++k) {
+        const double x = kN97X0 + kN97H * k;
+        const double s = std::exp(x);
+        const double z = -std::expm1(-s);
+        double lo = 0.0, hi = 1.0 / z + 1.0;
+        for (int it = 0; it < 2000; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (G_of(mid) > z) lo = mid;
+            else hi = mid;
+        }
+        const double A = 0.5 * (lo + hi);
+        f[k] = std::log(A * s);
+        dh[k] = kN97H * (1.0 + s * std::exp(-s) / (A * dG_of(A)));
+    }
+}
+
+}  // namespace mcc
+
 namespace {
 
 using mcc::StepArgs;
 
+constexpr size_t kTabOffset = 64;  // bytes into the context buffer where the N97 tables start
+constexpr size_t kTabDoubles = 2 * (mcc::kN97Nodes + 1);
+constexpr size_t kCtxBytes = kTabOffset + kTabDoubles * sizeof(double) + kTabDoubles * sizeof(float);
+
 constexpr size_t kStaticSmemReserve = 1024;  // margin above the cell kernel's static shared memory
-constexpr int kAutoCtasPerSm = 4;             // automatic tile: this many CTAs share one SM's shared memory
+#ifndef MCC_AUTO_CTAS
+#define MCC_AUTO_CTAS 4
+#endif
+constexpr int kAutoCtasPerSm = MCC_AUTO_CTAS;  // automatic tile: this many CTAs share one SM's shared memory
 constexpr int kMaxCtasPerSm = 2048 / mcc::kThreads;
 
 cudaStream_t S(mcc_stream s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -118,6 +189,11 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
     }
     a.status = ctx->dbuf;
     a.queue = ctx->dbuf + 1;
+    const char* base = reinterpret_cast<const char*>(ctx->dbuf) + kTabOffset;
+    a.n97_f = reinterpret_cast<const double*>(base);
+    a.n97_dh = a.n97_f + (mcc::kN97Nodes + 1);
+    a.n97_f32 = reinterpret_cast<const float*>(base + kTabDoubles * sizeof(double));
+    a.n97_dh32 = a.n97_f32 + (mcc::kN97Nodes + 1);
     return MCC_OK;
 }
 
@@ -181,7 +257,17 @@ int mcc_create(mcc_ctx** out, int device)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     c->smem_optin = (size_t)optin;
     c->num_sms = sms;
-    if (cudaMalloc(&c->dbuf, 64) != cudaSuccess || cudaMemset(c->dbuf, 0, 64) != cudaSuccess) {
+    // status word, queue counter and the N97 tables (double, then float), computed here once
+    double tab[kTabDoubles];
+    float tab32[kTabDoubles];
+    mcc::n97_table(tab, tab + (mcc::kN97Nodes + 1));
+    for (size_t k = 0; k < kTabDoubles; ++k) tab32[k] = (float)tab[k];
+    if (cudaMalloc(&c->dbuf, kCtxBytes) != cudaSuccess || cudaMemset(c->dbuf, 0, kTabOffset) != cudaSuccess ||
+        cudaMemcpy(reinterpret_cast<char*>(c->dbuf) + kTabOffset, tab, sizeof tab, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(reinterpret_cast<char*>(c->dbuf) + kTabOffset + sizeof tab, tab32, sizeof tab32,
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (c->dbuf) cudaFree(c->dbuf);
         delete c;
         return MCC_ERR_CUDA;
     }

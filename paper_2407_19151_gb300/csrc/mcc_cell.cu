@@ -82,6 +82,9 @@ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
+__device__ __forceinline__ void n97_tab(const StepArgs& A, N97Tab<double>& t) { t = {A.n97_f, A.n97_dh}; }
+__device__ __forceinline__ void n97_tab(const StepArgs& A, N97Tab<float>& t) { t = {A.n97_f32, A.n97_dh32}; }
+
 struct Shared {
     int off[kMaxSpecies + 1];
     int wmode[kMaxSpecies];  // weight order: 0 distinct (rho fixed for the visit), 1 all equal (rho = perm), 2 ties
@@ -285,7 +288,9 @@ __device__ __forceinline__ void rel_pair_dp_cm(const StepArgs& A, const InterCon
     V s = pick<V>(ic.kappa, ic.kappa_f) * wmax * (V)nmin / (cm.pmag * cm.pmag * cm.vrel);
     if (f & kPairTriplet) s *= (V)0.5;
     V st, omc, sp, cp, dx, dy, dz;
-    sample_angle<V>(A.method, s, U1, U4, st, omc);
+    N97Tab<V> tab;
+    n97_tab(A, tab);
+    sample_angle<V>(A.method, s, U1, U4, st, omc, tab);
     sincospi_v((V)2 * U2, &sp, &cp);
     rotate<V>(cm.px, cm.py, cm.pz, st, omc, cp, sp, dx, dy, dz);
     const V coef_b = cm.gC * cm.gC / (cc * cc * (cm.gC + (V)1));
@@ -330,7 +335,9 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
         V s = pick<V>(ic.kappa_mu2, ic.kappa_mu2_f) * wmax * (V)nmin / (u2 * um);
         if (f & kPairTriplet) s *= (V)0.5;
         V st, omc, sp, cp, dx, dy, dz;
-        sample_angle<V>(A.method, s, U1, U4, st, omc);
+        N97Tab<V> tab;
+        n97_tab(A, tab);
+        sample_angle<V>(A.method, s, U1, U4, st, omc, tab);
         sincospi_v((V)2 * U2, &sp, &cp);
         rotate<V>(ux, uy, uz, st, omc, cp, sp, dx, dy, dz);
         const V fa = pick<V>(ic.mu_ma, ic.mu_ma_f), fb = pick<V>(ic.mu_mb, ic.mu_mb_f);

@@ -431,23 +431,53 @@ __device__ __forceinline__ void n97_G_dG(float A, float& G, float& dG)
     dG = -(1.0f / (A * A) - (A < 40.0f ? 1.0f / (sh * sh) : 0.0f));
 }
 
+// Table of f(x) = ln(A s) over x = ln s in [kN97X0, kN97X0 + kN97Nodes * kN97H]: node k holds (f, h df/dx) for
+// cubic Hermite interpolation (error ~1e-9). Built on the host when a context is created.
+constexpr int kN97Nodes = 512;
+constexpr double kN97X0 = -6.907755278982137;  // ln 1e-3
+constexpr double kN97X1 = 2.4849066497880004;  // ln 12
+constexpr double kN97H = (kN97X1 - kN97X0) / kN97Nodes;
+
 template <class V>
-__device__ __forceinline__ V n97_A(V s)
+struct N97Tab {
+    const V* f;   // kN97Nodes + 1 values of ln(A s)
+    const V* dh;  // kN97Nodes + 1 values of h d ln(A s) / d ln s
+};
+
+// First approximation of A(s): below s = 1e-3, A = 1/(1 - e^-s) (exact to rounding there, since G(A) = 1/A up to
+// 2/expm1(2A) < e^-2000); above s = 12, the inversion A = 3y (1 + 3y^2/5) of L(A) = A/3 - A^3/45 with y = e^-s
+// (error O(y^5)); in between the table.
+template <class V>
+__device__ __forceinline__ V n97_A_table(V s, V z, const N97Tab<V>& tab)
+{
+    if (s < (V)1e-3) return (V)1 / z;
+    if (s > (V)12) {
+        const V y = (V)1 - z;
+        return (V)3 * y * ((V)1 + (V)0.6 * y * y);
+    }
+    const V u = (log(s) - (V)kN97X0) * (V)(1.0 / kN97H);
+    int k = (int)u;
+    k = k < 0 ? 0 : (k > kN97Nodes - 1 ? kN97Nodes - 1 : k);
+    const V t = u - (V)k;
+    const V f0 = tab.f[k], f1 = tab.f[k + 1], d0 = tab.dh[k], d1 = tab.dh[k + 1];
+    const V t2 = t * t, t3 = t2 * t;
+    const V f = ((V)2 * t3 - (V)3 * t2 + (V)1) * f0 + (t3 - (V)2 * t2 + t) * d0 + ((V)-2 * t3 + (V)3 * t2) * f1 +
+                (t3 - t2) * d1;
+    return exp(f) / s;
+}
+
+template <class V>
+__device__ __forceinline__ V n97_A(V s, const N97Tab<V>& tab)
 {
     const V z = -expm1(-s);                  // 1 - exp(-s)
     if (!(z < (V)1)) return (V)0;            // exp(-s) underflows: isotropic limit
     if (!(z > (V)0)) return (V)CUDART_INF;   // s == 0: no scattering
-    V A;
-    if (s < (V)1) {
-        A = (V)1 / z;                        // G(A) < 1/A: right of the root, tight for large A
-    } else {
-        const V t = (V)3 * ((V)1 - z);       // L(A) ~ A/3 - A^3/45 inverted to second order
-        A = t * ((V)1 + t * t / (V)15);
-    }
+    V A = n97_A_table<V>(s, z, tab);
+    if (sizeof(V) == 4) return A;            // ~1e-9 from the table: below float resolution
     // Newton converges quadratically: once a step is a few ulps the next would only chase rounding noise in G, so
     // stop there (a step of 4 ulps leaves an error far below one ulp).
-    const int iters = sizeof(V) == 8 ? 24 : 10;
-    const V tol = sizeof(V) == 8 ? (V)1e-15 : (V)5e-7;
+    const int iters = 6;
+    const V tol = (V)1e-15;
     for (int it = 0; it < iters; ++it) {
         V G, dG;
         n97_G_dG(A, G, dG);
@@ -465,7 +495,7 @@ __device__ __forceinline__ V n97_A(V s)
 //  N97:  1 - cos chi = -log1p(U1 expm1(-2A)) / A (inverse CDF of the density proportional to exp(A cos chi)),
 //        1 + cos chi = log1p((1 - U1) expm1(2A)) / A.
 template <class V>
-__device__ __forceinline__ void sample_angle(int method, V s, V U1, V U4, V& sin_t, V& omc)
+__device__ __forceinline__ void sample_angle(int method, V s, V U1, V U4, V& sin_t, V& omc, const N97Tab<V>& tab)
 {
     if (method == 0) {
         const V g = sqrt((V)-2 * log(U1)) * cospi((V)2 * U4);
@@ -482,7 +512,7 @@ __device__ __forceinline__ void sample_angle(int method, V s, V U1, V U4, V& sin
         }
         return;
     }
-    const V A = n97_A(s);
+    const V A = n97_A(s, tab);
     V o, q;
     if (A == (V)0) {
         o = (V)2 * U1;

@@ -39,6 +39,10 @@ struct StepArgs {
     double c, fE;
     float c_f, fE_f;
     RngKey rng;
+    const double* n97_f;   // N97 table (see mcc_device.cuh), double and float copies
+    const double* n97_dh;
+    const float* n97_f32;
+    const float* n97_dh32;
     // unfused input / output
     int32_t* pair_i;
     int32_t* pair_j;
@@ -58,6 +62,9 @@ struct StepArgs {
 
 // Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation, weight order).
 inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
+
+// N97 table: (f, h df/dx) at kN97Nodes + 1 nodes, computed on the host in double.
+void n97_table(double* f, double* dh);
 
 // Kernel launches (defined in mcc_cell.cu / mcc_bin.cu).
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
