@@ -205,6 +205,7 @@ def run_ours(args):
                            corr_pairs=corr, fail_count=fail)
 
     stream = torch.cuda.current_stream(dev)
+    tile = mcc.autotune_tile_cap(*v, w, off, C, S, species, wl.lnL, params, max_cell)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(dev)
@@ -267,6 +268,7 @@ def run_ours(args):
     # plain FP64 GPU step on the same workload (the comparison point of the mixed path)
     fp64 = None
     if args.fp64_steps > 0:
+        ctx.set_tile_cap(0)  # automatic tile for the double tile layout
         v64 = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev) for x in (wl.vx, wl.vy, wl.vz)]
         p64 = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
         mcc.mcc_step_fused(*v64, w, off, C, S, species, wl.lnL, p64, n_steps=1, max_cell=max_cell,
@@ -296,7 +298,7 @@ def run_ours(args):
         "config": {"workload": "three_species", "n_cells": C, "n_particles": N, "species": S,
                    "interactions": len(wl.interactions()), "pairs_per_step": pairs, "method": "N97",
                    "precision": "f32 velocities and kinematics, f64 weights, float-float sums, f64 coefficients",
-                   "max_cell": max_cell, "graph_steps": args.steps,
+                   "max_cell": max_cell, "graph_steps": args.steps, "tile_cap": tile or "auto",
                    "l2": "no flush: 4.3 GB state per step, far larger than the 129 MB L2",
                    "parallelism": f"cells, {world} independent shard(s)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -304,7 +306,7 @@ def run_ours(args):
                      "algorithmic_bytes": f"{BYTES_PER_PARTICLE['f32']} B/particle x {N} particles per launch"},
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": args.steps,  # one persistent step kernel per captured step
+        "gpu_launches": args.steps + 1,  # one persistent step kernel per captured step + the cell-order kernel
         "correction_failures": fails,
         "fp64_step": fp64,
         "cpu_baseline": cb,

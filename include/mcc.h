@@ -180,13 +180,14 @@ int mcc_correct(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* off
                 const mcc_params* params, const void* backup, int32_t* corr_pairs_out, int32_t* fail_flags_out,
                 mcc_stream stream);
 
-/* Bytes of device workspace mcc_step_fused needs when some cells exceed the shared-memory tile (max_cell
- * particles in the largest cell). Zero when every cell fits on chip. */
-int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t max_cell, size_t* bytes);
+/* Bytes of device workspace mcc_step_fused needs for n_cells cells of at most max_cell particles: the cells'
+ * processing order, plus per-CTA slabs when some cells exceed the on-chip tile. */
+int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t max_cell, size_t* bytes);
 
 /*
  * mcc_step_fused: n_steps whole collision steps (Algorithm 1 for every interaction in list order, each step with
- * index params->step + t) in one persistent kernel launch per step. Each CTA takes cells from a work queue, stages
+ * index params->step + t) in one persistent kernel launch per step. Each CTA takes cells from a work queue (largest
+ * cells first, ordered once per call by a small kernel), stages
  * the cell in shared memory (or in its workspace slab when the cell is larger than the on-chip tile), runs pairing,
  * scatter and correction for every interaction, and writes the cell back. The result equals the sequence
  * mcc_pair / mcc_scatter / mcc_correct over the interactions.
@@ -194,7 +195,7 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t max_cell, size_t
  *   max_cell       an upper bound on particles per cell (cells above it latch MCC_ERR_BOUNDS and are skipped)
  *   corr_pairs     [n_cells] device int32 or NULL: accumulated energy pairs
  *   fail_count     [n_cells] device int32 or NULL: accumulated failed corrections
- *   ws, ws_bytes   workspace of mcc_step_workspace_size bytes (may be NULL / 0 when that size is 0)
+ *   ws, ws_bytes   workspace of mcc_step_workspace_size bytes
  */
 int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* offsets, int32_t n_cells,
                    int32_t n_species, const mcc_species* sp, const double* lnL, const int32_t* interactions,

@@ -92,7 +92,7 @@ def lib():
                                   C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, P(_Params), vp, vp]),
         "mcc_correct": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), C.c_int32,
                                   C.c_int32, C.c_int32, P(_Params), vp, vp, vp, vp]),
-        "mcc_step_workspace_size": (C.c_int, [vp, C.c_int32, C.c_int32, P(C.c_size_t)]),
+        "mcc_step_workspace_size": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_step_fused": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), P(C.c_double),
                                      P(C.c_int32), C.c_int32, P(_Params), C.c_int32, C.c_int32, vp, vp, vp,
                                      C.c_size_t, vp]),
@@ -301,7 +301,8 @@ def mcc_step_fused(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, par
     if fail_count is None:
         fail_count = torch.zeros(max(n_cells, 1), dtype=torch.int32, device=vx.device)
     nb = C.c_size_t()
-    _check(lib().mcc_step_workspace_size(ctx.handle, P.prec, int(max_cell), C.byref(nb)), "mcc_step_workspace_size")
+    _check(lib().mcc_step_workspace_size(ctx.handle, P.prec, int(n_cells), int(max_cell), C.byref(nb)),
+           "mcc_step_workspace_size")
     ws = ctx.workspace(("step", P.prec), nb.value)
     cp = params._c()
     _check(lib().mcc_step_fused(ctx.handle, C.byref(P), _ptr(offsets), n_cells, n_species, _species(species),

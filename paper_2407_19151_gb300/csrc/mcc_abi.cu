@@ -91,7 +91,7 @@ constexpr size_t kCtxBytes = kTabOffset + kTabDoubles * sizeof(double) + kTabDou
 
 constexpr size_t kStaticSmemReserve = 1024;  // margin above the cell kernel's static shared memory
 #ifndef MCC_AUTO_CTAS
-#define MCC_AUTO_CTAS 4
+#define MCC_AUTO_CTAS 6
 #endif
 constexpr int kAutoCtasPerSm = MCC_AUTO_CTAS;  // automatic tile: this many CTAs share one SM's shared memory
 constexpr int kMaxCtasPerSm = 2048 / mcc::kThreads;
@@ -386,20 +386,32 @@ int mcc_correct(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
     return run_cells(ctx, a, f32, p->relativistic != 0, mcc::kCorrect, cap, S(stream));
 }
 
-int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t max_cell, size_t* bytes)
+namespace {
+// Workspace of mcc_step_fused: the cell order (n_cells int32, 256-aligned), then one slab per resident CTA for the
+// cells larger than the on-chip tile.
+size_t order_bytes(int32_t n_cells) { return ((size_t)n_cells * sizeof(int32_t) + 255) & ~(size_t)255; }
+
+int tile_of(const mcc_ctx* ctx, bool f32)
 {
-    if (!ctx || !bytes || max_cell < 0 || (prec != MCC_F64 && prec != MCC_F32_MIXED)) return MCC_ERR_INVALID_ARG;
-    const bool f32 = prec == MCC_F32_MIXED;
     const size_t capmax = max_tile_particles(ctx, f32);
-    const int tile = ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
-                                       : auto_tile(ctx, f32);
-    if (max_cell <= tile) {
-        *bytes = 0;
-        return MCC_OK;
-    }
-    const size_t stride = ((size_t)max_cell * mcc::tile_bytes_per_particle(f32) + 255) & ~(size_t)255;
-    // one slab per resident CTA (at most kMaxCtasPerSm per SM) for the cells larger than the on-chip tile
-    *bytes = stride * (size_t)ctx->num_sms * kMaxCtasPerSm;
+    return ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
+                             : auto_tile(ctx, f32);
+}
+
+size_t slab_stride_of(int32_t max_cell, bool f32)
+{
+    return ((size_t)max_cell * mcc::tile_bytes_per_particle(f32) + 255) & ~(size_t)255;
+}
+}  // namespace
+
+int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t max_cell, size_t* bytes)
+{
+    if (!ctx || !bytes || max_cell < 0 || n_cells < 0 || (prec != MCC_F64 && prec != MCC_F32_MIXED))
+        return MCC_ERR_INVALID_ARG;
+    const bool f32 = prec == MCC_F32_MIXED;
+    size_t total = order_bytes(n_cells);
+    if (max_cell > tile_of(ctx, f32)) total += slab_stride_of(max_cell, f32) * (size_t)ctx->num_sms * kMaxCtasPerSm;
+    *bytes = total;
     return MCC_OK;
 }
 
@@ -420,20 +432,23 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
     a.fail_count = fail_count;
     const bool f32 = P->prec == MCC_F32_MIXED;
     const bool rel = p->relativistic != 0;
-    const size_t capmax = max_tile_particles(ctx, f32);
-    const int tile = ctx->tile_cap > 0 ? (int)((size_t)ctx->tile_cap < capmax ? (size_t)ctx->tile_cap : capmax)
-                                       : auto_tile(ctx, f32);
+    size_t need = 0;
+    mcc_step_workspace_size(ctx, P->prec, n_cells, max_cell, &need);
+    if (!ws || ws_bytes < need) return MCC_ERR_WORKSPACE;
+    const int tile = tile_of(ctx, f32);
     const int cap = max_cell <= tile ? (max_cell > 0 ? max_cell : 1) : tile;
     int max_grid = 1 << 30;
+    int32_t* order = reinterpret_cast<int32_t*>(ws);
     if (max_cell > tile) {
-        size_t need = 0;
-        mcc_step_workspace_size(ctx, P->prec, max_cell, &need);
-        if (!ws || ws_bytes < need) return MCC_ERR_WORKSPACE;
-        a.slab = reinterpret_cast<char*>(ws);
-        a.slab_stride = (int64_t)(((size_t)max_cell * mcc::tile_bytes_per_particle(f32) + 255) & ~(size_t)255);
+        a.slab = reinterpret_cast<char*>(ws) + order_bytes(n_cells);
+        a.slab_stride = (int64_t)slab_stride_of(max_cell, f32);
         a.slab_cap = max_cell;
-        max_grid = (int)(ws_bytes / (size_t)a.slab_stride);
+        max_grid = (int)((ws_bytes - order_bytes(n_cells)) / (size_t)a.slab_stride);
     }
+    // largest cells first (the order is the same for every step of the call)
+    if (mcc::launch_cell_order(offsets, n_cells, n_species, order, S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
+    ctx->launches += 1;
+    a.order = order;
     for (int32_t t = 0; t < n_steps; ++t) {
         a.rng.step = (uint32_t)(p->step + (uint64_t)t);
         rc = run_cells(ctx, a, f32, rel, mcc::kFused, cap, S(stream), max_grid);

@@ -18,7 +18,7 @@
 #include "mcc_kernels.h"
 
 #ifndef MCC_MIN_BLOCKS
-#define MCC_MIN_BLOCKS 4
+#define MCC_MIN_BLOCKS 6
 #endif
 
 namespace mcc {
@@ -822,12 +822,48 @@ __global__ void __launch_bounds__(kThreads, MCC_MIN_BLOCKS) cell_kernel(const __
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ Shared sh;
     for (;;) {
-        if (threadIdx.x == 0) sh.cell = atomicAdd(A.queue, 1);
+        if (threadIdx.x == 0) {
+            const int q = atomicAdd(A.queue, 1);
+            sh.cell = (q < A.n_cells && A.order) ? A.order[q] : q;
+        }
         __syncthreads();
         const int c = sh.cell;
         if (c >= A.n_cells) break;
         process_cell<V, REL, MODE>(A, c, dyn, sh);
         __syncthreads();
+    }
+}
+
+// Cells ordered by descending size class (floor(log2 n)), so the persistent CTAs take the largest cells first and
+// the small ones fill in at the end (longest-processing-time order). Order within a class is arbitrary: cells are
+// independent, so the result does not depend on it. One CTA; shared-memory counters.
+constexpr int kOrderThreads = 1024;
+
+__global__ void __launch_bounds__(kOrderThreads) k_cell_order(const int64_t* __restrict__ offsets, int32_t n_cells,
+                                                             int32_t S, int32_t* __restrict__ order)
+{
+    __shared__ int hist[33];
+    if (threadIdx.x < 33) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_cells; c += kOrderThreads) {
+        const int64_t n = offsets[(int64_t)(c + 1) * S] - offsets[(int64_t)c * S];
+        const int cls = n > 0 ? 63 - __clzll((unsigned long long)n) : 0;
+        atomicAdd(&hist[32 - (cls > 32 ? 32 : cls)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 33; ++b) {
+            const int x = hist[b];
+            hist[b] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_cells; c += kOrderThreads) {
+        const int64_t n = offsets[(int64_t)(c + 1) * S] - offsets[(int64_t)c * S];
+        const int cls = n > 0 ? 63 - __clzll((unsigned long long)n) : 0;
+        order[atomicAdd(&hist[32 - (cls > 32 ? 32 : cls)], 1)] = c;
     }
 }
 
@@ -877,6 +913,12 @@ int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem)
         cudaSuccess)
         return 0;
     return blocks;
+}
+
+cudaError_t launch_cell_order(const int64_t* offsets, int32_t n_cells, int32_t S, int32_t* order, cudaStream_t st)
+{
+    k_cell_order<<<1, kOrderThreads, 0, st>>>(offsets, n_cells, S, order);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st)

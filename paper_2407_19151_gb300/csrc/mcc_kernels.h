@@ -54,6 +54,7 @@ struct StepArgs {
     // control
     int32_t* status;
     int32_t* queue;
+    const int32_t* order;  // processing order of the cells (null: index order)
     int32_t cap;        // particles per cell staged in shared memory
     char* slab;         // per-CTA global slabs for larger cells (may be null)
     int64_t slab_stride;
@@ -68,6 +69,7 @@ void n97_table(double* f, double* dh);
 
 // Kernel launches (defined in mcc_cell.cu / mcc_bin.cu).
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_cell_order(const int64_t* offsets, int32_t n_cells, int32_t S, int32_t* order, cudaStream_t st);
 int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem);
 cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem);
 size_t cell_kernel_static_smem(bool f32, bool rel, int mode);
