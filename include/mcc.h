@@ -73,7 +73,8 @@ typedef struct {
 /* Step parameters. dt, dV, eps0 enter the scattering length of Eq. sab_TA77; c is used in relativistic mode;
  * fE is the energy-correction factor of Eq. U_inelastic; sort_by_weight is the optional sort of Algorithm 1;
  * max_corr_passes bounds the energy-pair passes; correct = 0 runs the scatter alone. seed keys the random stream;
- * step is the time-step index that enters every random counter (taken modulo 2^32). */
+ * step is the time-step index that enters every random counter (taken modulo 2^32); cell_base offsets the cell
+ * counter for sharded runs (0 for a whole problem). */
 typedef struct {
     int32_t method;       /* mcc_method */
     int32_t relativistic; /* 0 or 1 */
@@ -84,6 +85,8 @@ typedef struct {
     int32_t correct;
     uint64_t seed;
     uint64_t step;
+    uint32_t cell_base; /* global id of the first cell (the random counters use global cell ids, so a shard of
+                           cells [cell_base, cell_base + n_cells) draws exactly what the unsharded run draws) */
 } mcc_params;
 
 /* Create / destroy a context on `device`. The context owns only a small device buffer (status word, work-queue

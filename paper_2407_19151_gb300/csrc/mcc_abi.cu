@@ -186,6 +186,7 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
         a.rng.k0 = (uint32_t)p->seed;
         a.rng.k1 = (uint32_t)(p->seed >> 32);
         a.rng.step = (uint32_t)p->step;
+        a.rng.cell_base = p->cell_base;
     }
     a.status = ctx->dbuf;
     a.queue = ctx->dbuf + 1;

@@ -37,6 +37,7 @@ __device__ __forceinline__ void latch(int* status, int code)
 // ---------------------------------------------------------------------------------------------------------------
 struct RngKey {
     uint32_t k0, k1, step;
+    uint32_t cell_base;  // global id of local cell 0
 };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
@@ -64,7 +65,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
 __device__ __forceinline__ uint4 draw(const RngKey& k, uint32_t index, uint32_t cell, uint32_t inter,
                                       uint32_t purpose)
 {
-    return philox4x32_10(index, cell, k.step, (inter << 8) | purpose, k.k0, k.k1);
+    return philox4x32_10(index, cell + k.cell_base, k.step, (inter << 8) | purpose, k.k0, k.k1);
 }
 
 // Uniform on (0, 1): ((r >> 9) + 1/2) 2^-23, exact in float and double.
