@@ -88,6 +88,7 @@ __device__ __forceinline__ void n97_tab(const StepArgs& A, N97Tab<float>& t) { t
 struct Shared {
     int off[kMaxSpecies + 1];
     int wmode[kMaxSpecies];  // weight order: 0 distinct (rho fixed for the visit), 1 all equal (rho = perm), 2 ties
+                             // (sorted per interaction), 3 stored in strictly descending order (rho = identity)
     int cell;
     int fail;
     alignas(16) unsigned char red_raw[8 * kThreads * 8];  // block_sum partials (8 quantities x 8 bytes)
@@ -99,6 +100,8 @@ struct Shared {
     double B[3];
     float Bf[3];
     double D[2];
+    double W1[kMaxSpecies];  // per species sum of w over the cell (static for the visit)
+    double W2[kMaxSpecies];  // per species sum of w^2
 };
 
 constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp in registers
@@ -279,6 +282,31 @@ __device__ __forceinline__ bool heavy_moves(const Tile<float>& t, const StepArgs
     return u23<double>(r) * fmax(wi, wj) < fmin(wi, wj);
 }
 
+// acc += w_i (x_new - x_old): on the mixed path the difference as float-float (two_sum, exact) times the weight's
+// hi/lo split
+__device__ __forceinline__ void add_weighted_change(Acc<double>& acc, const Tile<double>& t, int i, double xn,
+                                                    double xo)
+{
+    acc.add(t.w[i] * (xn - xo));
+}
+__device__ __forceinline__ void add_weighted_change(Acc<float>& acc, const Tile<float>& t, int i, float xn, float xo)
+{
+    const float2 w = t.w[i];
+    acc.add(ff_mul({w.x, w.y}, ff_two_sum(xn, -xo)));
+}
+
+__device__ __forceinline__ void add_weight_sums(Acc<double>& a1, Acc<double>& a2, const Tile<double>& t, int i)
+{
+    a1.add(t.w[i]);
+    a2.add(t.w[i] * t.w[i]);
+}
+__device__ __forceinline__ void add_weight_sums(Acc<float>& a1, Acc<float>& a2, const Tile<float>& t, int i)
+{
+    const ff w = {t.w[i].x, t.w[i].y};
+    a1.add(w);
+    a2.add(ff_mul(w, w));
+}
+
 // Relativistic pair, given its CM frame: scattering length with |p*|^2 v_rel* in place of mu^2 u^3, rotation of p*
 // through (Theta, phi), boost of the change back to the lab frame. Returns dp = p_i' - p_i.
 template <class V>
@@ -380,14 +408,12 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
         else upd_j = moves;
     }
     if (upd_i) {
-        t.v[i] = vi[0] + dvi[0];
-        t.v[cap + i] = vi[1] + dvi[1];
-        t.v[2 * cap + i] = vi[2] + dvi[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) t.v[d * cap + i] = vi[d] + dvi[d];
     }
     if (upd_j) {
-        t.v[j] = vj[0] + dvj[0];
-        t.v[cap + j] = vj[1] + dvj[1];
-        t.v[2 * cap + j] = vj[2] + dvj[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) t.v[d * cap + j] = vj[d] + dvj[d];
     }
 }
 
@@ -400,6 +426,29 @@ __device__ __forceinline__ bool fast_pair(V c, const V v1[3], const V v2[3])
     return (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]) > lim || (v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]) > lim;
 }
 
+// Energy-pair order of a species segment with partially tied weights: the interaction's random permutation, stably
+// sorted by descending weight (keys: weight, rank in the permutation). Out of line: rare.
+template <class V>
+__device__ __noinline__ void tie_order(const StepArgs& A, const Tile<V>& t, int64_t cs, int s0, int ns)
+{
+    if (ns <= kWarpSortMax) {
+        if (threadIdx.x < 32) {
+            for (int r = threadIdx.x; r < ns; r += 32)
+                t.keys[s0 + r] = weight_key(w_exact(t, A, cs, t.perm[s0 + r]), (uint32_t)r);
+            warp_sort_buf(t.keys + s0, ns);
+            for (int m = threadIdx.x; m < ns; m += 32) t.rho[s0 + m] = t.perm[s0 + (int)(t.keys[s0 + m] & kPermMask)];
+        }
+        __syncthreads();
+    } else {
+        for (int q = threadIdx.x; q < ns; q += kThreads)
+            t.keys[s0 + q] = weight_key(w_exact(t, A, cs, t.perm[s0 + q]), (uint32_t)q);
+        __syncthreads();
+        block_sort_u64(t.keys + s0, ns);
+        for (int q = threadIdx.x; q < ns; q += kThreads) t.rho[s0 + q] = t.perm[s0 + (int)(t.keys[s0 + q] & kPermMask)];
+        __syncthreads();
+    }
+}
+
 // Moment correction of one interaction (Sec. 4, Appendix A, Sec. 5.2).
 template <class V, bool REL, int MODE>
 __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int c, int64_t cs,
@@ -409,61 +458,41 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
     const int nside = intra ? 1 : 2;
     const V cc = pick<V>(A.c, A.c_f);
 
-    // Eq. vp_pm: per species sums of w (v - v_bs) and w^2 (times m_s later, in FP64)
+    // Eq. vp_pm: per species sums of w (v_ps - v_bs), times m_s in FP64; the sums of w^2 are fixed for the visit
     {
-        Acc<V> acc[8];
+        Acc<V> mom[6];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) acc[m] = Acc<V>::zero();
+        for (int m = 0; m < 6; ++m) mom[m] = Acc<V>::zero();
         for (int side = 0; side < nside; ++side) {
             const int s0 = side ? b0 : a0, ns = side ? nb : na;
             for (int q = threadIdx.x; q < ns; q += kThreads) {
                 const int i = s0 + q;
-                if constexpr (sizeof(V) == 8) {
-                    const double w = t.w[i];
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) acc[side * 4 + d].add(w * (t.v[d * cap + i] - t.vb[d * cap + i]));
-                    acc[side * 4 + 3].add(w * w);
-                } else {
-                    const float2 w = t.w[i];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const ff dd = ff_two_sum(t.v[d * cap + i], -t.vb[d * cap + i]);
-                        acc[side * 4 + d].add(ff_mul({w.x, w.y}, dd));
-                    }
-                    acc[side * 4 + 3].add(ff_mul({w.x, w.y}, {w.x, w.y}));
-                }
+                for (int d = 0; d < 3; ++d)
+                    add_weighted_change(mom[side * 3 + d], t, i, t.v[d * cap + i], t.vb[d * cap + i]);
             }
         }
-        block_sum<V, 8>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
+        block_sum<V, 6>(mom, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
         if (threadIdx.x == 0) {
             const double* r = sh.red;
             const double ma = A.m[ic.a], mb = A.m[ic.b];
-            const double Sw = ma * r[3] + (intra ? 0.0 : mb * r[7]);
+            const double Sw = ma * sh.W2[ic.a] + (intra ? 0.0 : mb * sh.W2[ic.b]);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const double S = ma * r[d] + (intra ? 0.0 : mb * r[4 + d]);
+                const double S = ma * r[d] + (intra ? 0.0 : mb * r[3 + d]);
                 sh.B[d] = S / Sw;
                 sh.Bf[d] = (float)sh.B[d];
             }
         }
         __syncthreads();
-        for (int side = 0; side < nside; ++side) {
-            const int s0 = side ? b0 : a0, ns = side ? nb : na;
-            for (int q = threadIdx.x; q < ns; q += kThreads) {
-                const int i = s0 + q;
-                const V w = wv(t, i);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) t.v[d * cap + i] -= pick<V>(sh.B[d], sh.Bf[d]) * w;
-            }
-        }
-        __syncthreads();
     }
 
-    // Eq. Econs as per-particle energy differences, post-shift species energies and weight sums (Eq. DeltaEs)
+    // Momentum shift (Eq. vp_pm) fused with the sums of Eq. Econs as per-particle energy differences and the
+    // post-shift species energies (Eq. DeltaEs; its weight sums are fixed for the visit)
     {
-        Acc<V> acc[6];
+        Acc<V> acc[4];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) acc[m] = Acc<V>::zero();
+        for (int m = 0; m < 4; ++m) acc[m] = Acc<V>::zero();
         for (int side = 0; side < nside; ++side) {
             const int s0 = side ? b0 : a0, ns = side ? nb : na;
             for (int q = threadIdx.x; q < ns; q += kThreads) {
@@ -472,36 +501,36 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 V dd = 0, v2 = 0, b2 = 0;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    const V x = t.v[d * cap + i], y = t.vb[d * cap + i];
+                    const V x = t.v[d * cap + i] - pick<V>(sh.B[d], sh.Bf[d]) * w;  // v_pm = v_ps - B w_p
+                    t.v[d * cap + i] = x;
+                    const V y = t.vb[d * cap + i];
                     dd += (x - y) * (x + y);
                     v2 += x * x;
                     b2 += y * y;
                 }
                 if (!REL) {
-                    acc[side * 3 + 0].add((V)0.5 * w * dd);
-                    acc[side * 3 + 1].add((V)0.5 * w * v2);
+                    acc[side * 2 + 0].add((V)0.5 * w * dd);
+                    acc[side * 2 + 1].add((V)0.5 * w * v2);
                 } else {
                     const V c2 = cc * cc;
                     const V ga = sqrt((V)1 + v2 / c2), gb = sqrt((V)1 + b2 / c2);
-                    acc[side * 3 + 0].add(w * dd / (ga + gb));
-                    acc[side * 3 + 1].add(w * v2 / (ga + (V)1));
+                    acc[side * 2 + 0].add(w * dd / (ga + gb));
+                    acc[side * 2 + 1].add(w * v2 / (ga + (V)1));
                 }
-                if constexpr (sizeof(V) == 8) acc[side * 3 + 2].add(w);
-                else acc[side * 3 + 2].add(ff{t.w[i].x, t.w[i].y});
             }
         }
-        block_sum<V, 6>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
+        block_sum<V, 4>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
         if (threadIdx.x == 0) {
             const double* r = sh.red;
             const double ma = A.m[ic.a], mb = A.m[ic.b];
-            const double dE = ma * r[0] + (intra ? 0.0 : mb * r[3]);
+            const double dE = ma * r[0] + (intra ? 0.0 : mb * r[2]);
             double D0 = dE, D1 = 0.0;
             int fail = 0;
             if (!intra) {
                 const bool can0 = na >= 2, can1 = nb >= 2;
                 if (can0 && can1) {
-                    const double wa = r[2] / (double)na * (ma * r[1]);
-                    const double wb = r[5] / (double)nb * (mb * r[4]);
+                    const double wa = sh.W1[ic.a] / (double)na * (ma * r[1]);
+                    const double wb = sh.W1[ic.b] / (double)nb * (mb * r[3]);
                     const double den = wa + wb;
                     if (den > 0.0) {
                         D0 = wa / den * dE;
@@ -520,7 +549,7 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
             }
             // |Delta E_s| at or below 64 ulps (double) of species s's post-shift kinetic energy counts as zero
             sh.D[0] = fabs(D0) <= 0x1p-47 * (ma * r[1]) ? 0.0 : D0;
-            sh.D[1] = fabs(D1) <= 0x1p-47 * (intra ? 0.0 : mb * r[4]) ? 0.0 : D1;
+            sh.D[1] = fabs(D1) <= 0x1p-47 * (intra ? 0.0 : mb * r[3]) ? 0.0 : D1;
             sh.fail = fail;
         }
         __syncthreads();
@@ -539,28 +568,9 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
         // Algorithm 1). Distinct weights: the order fixed at the cell's load; all equal: the permutation itself;
         // partial ties: sorted here by (weight, rank in the permutation).
         const int mode = A.sort_by_weight ? sh.wmode[spc] : 1;
-        if (mode == 2) {
-            if (ns <= kWarpSortMax) {
-                if (threadIdx.x < 32) {
-                    for (int r = threadIdx.x; r < ns; r += 32)
-                        t.keys[s0 + r] = weight_key(w_exact(t, A, cs, t.perm[s0 + r]), (uint32_t)r);
-                    warp_sort_buf(t.keys + s0, ns);
-                    for (int m = threadIdx.x; m < ns; m += 32)
-                        t.rho[s0 + m] = t.perm[s0 + (int)(t.keys[s0 + m] & kPermMask)];
-                }
-                __syncthreads();
-            } else {
-                for (int q = threadIdx.x; q < ns; q += kThreads)
-                    t.keys[s0 + q] = weight_key(w_exact(t, A, cs, t.perm[s0 + q]), (uint32_t)q);
-                __syncthreads();
-                block_sort_u64(t.keys + s0, ns);
-                for (int q = threadIdx.x; q < ns; q += kThreads)
-                    t.rho[s0 + q] = t.perm[s0 + (int)(t.keys[s0 + q] & kPermMask)];
-                __syncthreads();
-            }
-        }
+        if (mode == 2) tie_order<V>(A, t, cs, s0, ns);
         const int32_t* order = (mode == 1) ? t.perm : t.rho;
-        auto rho = [&](int m) -> int { return order[s0 + m]; };
+        auto rho = [&](int m) -> int { return mode == 3 ? s0 + m : order[s0 + m]; };
         V Dabs = (V)fabs(D);
         const V sgn = D > 0.0 ? (V)1 : (V)-1;
         const V fE = pick<V>(A.fE, A.fE_f);
@@ -717,38 +727,64 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
                 pair_at(t, intra, na, nb, a0, b0, p, i, j, f);
             }
         };
-        if (intra) {
-            const bool odd = (na & 1) != 0;
-            if (odd && threadIdx.x == 0) {
-                for (int p = 0; p < 3; ++p) {  // the triplet shares particles: in order, one thread
-                    int i, j;
-                    uint8_t f;
-                    get(p, i, j, f);
-                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
-                }
-            }
-            for (int p = (odd ? 3 : 0) + (int)threadIdx.x; p < npairs; p += kThreads) {
+        // Intra: one round; an odd count starts with the triplet (pairs 0..2 share particles), run in order by thread
+        // 0 while the other threads start on pair 3. Inter: rounds of N_min disjoint pairs, in order. One call site
+        // keeps a single inlined copy of the pair code.
+        const int lead = (intra && (na & 1)) ? 3 : 0;
+        const int round = intra ? npairs : nmin;
+        for (int r0 = 0; r0 < npairs; r0 += round) {
+            const int r1 = r0 + round < npairs ? r0 + round : npairs;
+            int p = (lead && threadIdx.x == 0) ? 0 : r0 + lead + (int)threadIdx.x;
+            while (p < r1) {
                 int i, j;
                 uint8_t f;
                 get(p, i, j, f);
                 scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
+                p = (p + 1 < lead) ? p + 1 : (p < lead ? lead + (int)threadIdx.x : p + kThreads);
             }
             __syncthreads();
-        } else {
-            for (int r0 = 0; r0 < npairs; r0 += nmin) {  // rounds of N_min disjoint pairs, in order
-                const int r1 = (r0 + nmin < npairs) ? r0 + nmin : npairs;
-                for (int p = r0 + (int)threadIdx.x; p < r1; p += kThreads) {
-                    int i, j;
-                    uint8_t f;
-                    get(p, i, j, f);
-                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
-                }
-                __syncthreads();
-            }
         }
     }
     if (MODE == kCorrect || (MODE == kFused && A.correct))
         correct_interaction<V, REL, MODE>(A, t, sh, c, cs, ic, intra, a0, na, b0, nb);
+}
+
+// Weight-descending order of each species of the cell, fixed for this visit when the weight keys are distinct (one
+// warp per species). A segment stored with strictly increasing keys (strictly descending weights, no two within the
+// key's tie width) needs no sort (wmode 3). Out of line: it runs once per visit and keeps the per-interaction code
+// compact.
+template <class V>
+__device__ __noinline__ void weight_order(const StepArgs& A, const Tile<V>& t, Shared& sh, int64_t cs, int S)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int sp = 0; sp < S; ++sp) {
+        const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
+        if (warp != sp % kWarps) continue;
+        bool unsorted = false;
+        for (int q0 = 0; q0 + 1 < ns && !unsorted; q0 += 32) {
+            const int q = q0 + lane;
+            const bool bad = q + 1 < ns &&
+                             weight_key(w_exact(t, A, cs, s0 + q), 0) >= weight_key(w_exact(t, A, cs, s0 + q + 1), 0);
+            unsorted = __any_sync(0xffffffffu, bad);
+        }
+        if (!unsorted) {
+            if (lane == 0) sh.wmode[sp] = 3;
+            continue;
+        }
+        if (ns > kWarpSortMax) {
+            if (lane == 0) sh.wmode[sp] = 2;
+            continue;
+        }
+        int tie = 0;
+        for (int q = lane; q < ns; q += 32) t.keys[s0 + q] = weight_key(w_exact(t, A, cs, s0 + q), (uint32_t)q);
+        warp_sort_buf(t.keys + s0, ns);
+        for (int q = lane; q < ns; q += 32) t.rho[s0 + q] = s0 + (int)(t.keys[s0 + q] & kPermMask);
+        for (int q = lane; q + 1 < ns; q += 32) tie |= (t.keys[s0 + q] >> kPermBits) == (t.keys[s0 + q + 1] >> kPermBits);
+        tie = __any_sync(0xffffffffu, tie);
+        const bool all_equal = (t.keys[s0] >> kPermBits) == (t.keys[s0 + ns - 1] >> kPermBits);
+        if (lane == 0) sh.wmode[sp] = all_equal ? 1 : (tie ? 2 : 0);
+    }
+    __syncthreads();
 }
 
 template <class V, bool REL, int MODE>
@@ -781,31 +817,28 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
         }
     }
     __syncthreads();
-    // weight-descending order of each species, fixed for this visit when the (truncated) weights are distinct
-    if ((MODE == kFused || MODE == kCorrect) && A.sort_by_weight) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int sp = 0; sp < S; ++sp) {
-            const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
-            if (ns > kWarpSortMax) {
-                if (threadIdx.x == 0) sh.wmode[sp] = 2;
-                continue;
+    // per species sums of w and w^2 (Eq. vp_pm denominator, Eq. DeltaEs mean weights), once per visit
+    if (MODE == kFused || MODE == kCorrect) {
+        for (int sp0 = 0; sp0 < S; sp0 += 4) {
+            Acc<V> acc[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[m] = Acc<V>::zero();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int sp = sp0 + k;
+                if (sp >= S) break;
+                const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
+                for (int q = threadIdx.x; q < ns; q += kThreads) add_weight_sums(acc[2 * k], acc[2 * k + 1], t, s0 + q);
             }
-            if (warp != sp % kWarps) continue;
-            if (ns < 2) {
-                if (lane == 0) sh.wmode[sp] = 0;
-                continue;
+            block_sum<V, 8>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
+            if (threadIdx.x < 4 && sp0 + (int)threadIdx.x < S) {
+                sh.W1[sp0 + threadIdx.x] = sh.red[2 * threadIdx.x];
+                sh.W2[sp0 + threadIdx.x] = sh.red[2 * threadIdx.x + 1];
             }
-            int tie = 0;
-            for (int q = lane; q < ns; q += 32) t.keys[s0 + q] = weight_key(w_exact(t, A, cs, s0 + q), (uint32_t)q);
-            warp_sort_buf(t.keys + s0, ns);
-            for (int q = lane; q < ns; q += 32) t.rho[s0 + q] = s0 + (int)(t.keys[s0 + q] & kPermMask);
-            for (int q = lane; q + 1 < ns; q += 32) tie |= (t.keys[s0 + q] >> kPermBits) == (t.keys[s0 + q + 1] >> kPermBits);
-            tie = __any_sync(0xffffffffu, tie);
-            const bool all_equal = (t.keys[s0] >> kPermBits) == (t.keys[s0 + ns - 1] >> kPermBits);
-            if (lane == 0) sh.wmode[sp] = all_equal ? 1 : (tie ? 2 : 0);
         }
         __syncthreads();
     }
+    if ((MODE == kFused || MODE == kCorrect) && A.sort_by_weight) weight_order<V>(A, t, sh, cs, S);
     for (int k = 0; k < A.n_inter; ++k) interaction<V, REL, MODE>(A, t, sh, c, cs, k);
     if (MODE != kPair) {
         for (int i = threadIdx.x; i < n; i += kThreads) {

@@ -96,6 +96,17 @@ class Workload:
                 tot += int(np.where((na > 0) & (nb > 0), np.maximum(na, nb), 0).sum())
         return tot
 
+    def weight_ordered(self) -> "Workload":
+        """The same particles with each (cell, species) segment stored by descending weight (equal weights keep
+        their order): the layout in which the optional weight order of the energy correction is the identity."""
+        off = self.offsets
+        seg = np.repeat(np.arange(len(off) - 1, dtype=np.int64), np.diff(off))
+        order = np.lexsort((np.arange(self.n, dtype=np.int64), -self.w, seg))
+        return Workload(self.name, self.n_cells, self.q, self.m, self.lnL, self.counts.copy(), self.vx[order],
+                        self.vy[order], self.vz[order], self.w[order], self.dt, self.method, self.relativistic,
+                        self.fE, self.precision, self.n_steps, self.seed, self.dV, self.eps0, self.c,
+                        dict(self.meta, weight_ordered=True))
+
     def subset(self, n_cells: int) -> "Workload":
         """The first ``n_cells`` cells (cell ids, and hence every random draw, are unchanged)."""
         k = min(int(n_cells), self.n_cells)

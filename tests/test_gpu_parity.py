@@ -148,7 +148,19 @@ FUSED_F64 = [
     ("relativistic", lambda: W.relativistic_beam(n_cells=40, count_lo=16, count_hi=300, precision="f64"), {}),
     ("tied_weights", lambda: _tied(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
     ("large_segments", lambda: W.differentiable(n_cells=4, per_species=1500), {}),
+    ("weight_ordered", lambda: W.three_species(n_cells=64, mean_count=90, precision="f64").weight_ordered(), {}),
+    ("ordered_key_ties", lambda: _key_ties(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
 ]
+
+
+def _key_ties(wl):
+    """Weight-ordered segments whose weights fall strictly but only below the sort key's 2^-32 tie width: the
+    stored order is not the weight order (ties keep the random order), so the kernel must sort."""
+    off = wl.offsets
+    for k in range(len(off) - 1):
+        n = int(off[k + 1] - off[k])
+        wl.w[off[k]:off[k + 1]] = 3.0 * (1.0 + 2.0 ** -40 * np.arange(n, 0, -1))
+    return wl
 
 
 def _tied(wl):
@@ -186,6 +198,7 @@ FUSED_F32 = [
      F32_TOL, 2e-4),
     ("three_species", lambda: W.three_species(n_cells=200, mean_count=120), F32_TOL, 2e-4),
     ("three_species_ta77", lambda: W.three_species(n_cells=200, mean_count=120, method=W.TA77), F32_TOL, 2e-4),
+    ("three_species_ordered", lambda: W.three_species(n_cells=200, mean_count=120).weight_ordered(), F32_TOL, 2e-4),
     ("relativistic", lambda: W.relativistic_beam(n_cells=100, count_lo=16, count_hi=400), 5e-5, 2e-3),
 ]
 
