@@ -85,6 +85,7 @@ def lib():
         sig = {
             "orc_philox4x32_10": (None, [u32, u32, u32]),
             "orc_bin": (C.c_int, [i32, i32, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
+            "orc_bin_weighted": (C.c_int, [i32, i32, d, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
             "orc_permutation": (C.c_int, [C.c_int64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                           i32]),
             "orc_pairs": (C.c_int, [i64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -136,6 +137,18 @@ def bin_particles(cell, species, n_cells: int, n_species: int):
     offsets = np.zeros(n_cells * n_species + 1, dtype=np.int64)
     _check(lib().orc_bin(_p(cell, C.c_int32), _p(species, C.c_int32), len(cell), n_cells, n_species,
                          _p(perm, C.c_int32), _p(offsets, C.c_int64)), "bin")
+    return perm, offsets
+
+
+def bin_particles_weighted(cell, species, w, n_cells: int, n_species: int):
+    """Cell sort with every segment in the weight-sort order of Algorithm 1 (see orc_bin_weighted)."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    perm = np.zeros(len(cell), dtype=np.int32)
+    offsets = np.zeros(n_cells * n_species + 1, dtype=np.int64)
+    _check(lib().orc_bin_weighted(_p(cell, C.c_int32), _p(species, C.c_int32), _p(w, C.c_double), len(cell),
+                                  n_cells, n_species, _p(perm, C.c_int32), _p(offsets, C.c_int64)), "bin_weighted")
     return perm, offsets
 
 

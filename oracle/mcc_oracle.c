@@ -588,6 +588,39 @@ static uint64_t weight_key(double w, uint32_t rank)
     return (~b & ~(uint64_t)(PERM_MAX_N - 1)) | (uint64_t)rank;
 }
 
+/* Cell sort with each segment stored in the order of the optional weight sort of Algorithm 1: orc_bin, then
+ * within every (cell, species) segment the stable order by the weight key above (descending weight; weights that
+ * agree to 2^-32 relative keep increasing particle index). In this layout the weight order of a segment whose keys
+ * are all distinct is the identity. */
+int orc_bin_weighted(const int32_t* cell, const int32_t* species, const double* w, int64_t n, int32_t n_cells,
+                     int32_t n_species, int32_t* perm_out, int64_t* offsets_out)
+{
+    int rc = orc_bin(cell, species, n, n_cells, n_species, perm_out, offsets_out);
+    if (rc != 0) return rc;
+    int64_t nk = (int64_t)n_cells * n_species;
+    for (int64_t k = 0; k < nk; ++k) {
+        int64_t b = offsets_out[k], len = offsets_out[k + 1] - b;
+        if (len < 2) continue;
+        if (len > PERM_MAX_N) return -1;
+        uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)len);
+        int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)len);
+        if (!keys || !idx) {
+            free(keys);
+            free(idx);
+            return -2;
+        }
+        for (int64_t r = 0; r < len; ++r) {
+            idx[r] = perm_out[b + r];
+            keys[r] = weight_key(w[idx[r]], (uint32_t)r);
+        }
+        qsort(keys, (size_t)len, sizeof(uint64_t), cmp_u64);
+        for (int64_t r = 0; r < len; ++r) perm_out[b + r] = idx[keys[r] & (PERM_MAX_N - 1)];
+        free(keys);
+        free(idx);
+    }
+    return 0;
+}
+
 /* Kinetic energy of one particle of mass mp (weighted) with state v (velocity or proper velocity). */
 static double ke(int rel, double c, double mp, const double v[3])
 {

@@ -9,6 +9,7 @@
  * Parity status per function (pins live in tests/test_oracle_*.py):
  *   orc_philox4x32_10      pinned: published Philox-4x32-10 known-answer values.
  *   orc_bin                pinned: equals a stable library sort by (cell, species).
+ *   orc_bin_weighted       pinned: equals a library lexicographic sort by (cell, species, truncated weight, index).
  *   orc_pairs              pinned: brute-force structure checks and pairing-uniformity chi-square.
  *   orc_n97_A / angles     pinned: E[cos chi] = exp(-s) by quadrature, asymptotic limits, TA77 variance.
  *   orc_scatter            pinned: expected drag of Eqs. sb_TA_weighted / sa_TA77_weighted, isotropisation and
@@ -46,6 +47,9 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 
 int orc_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
             int32_t* perm_out, int64_t* offsets_out);
+
+int orc_bin_weighted(const int32_t* cell, const int32_t* species, const double* w, int64_t n, int32_t n_cells,
+                     int32_t n_species, int32_t* perm_out, int64_t* offsets_out);
 
 int orc_permutation(int64_t n, uint64_t seed, uint64_t step, uint32_t cell, uint32_t inter, uint32_t side,
                     int32_t* perm_out);

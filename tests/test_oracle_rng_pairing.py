@@ -56,6 +56,30 @@ def test_bin_equals_stable_sort():
     np.testing.assert_array_equal(off, np.concatenate([[0], np.cumsum(np.bincount(key, minlength=C * S))]))
 
 
+def test_bin_weighted_equals_lexicographic_sort():
+    """Each segment ordered by descending weight truncated to 32 fraction bits (frexp: same exponent and the same
+    floor of the fraction times 2^32 tie), ties by increasing particle index; segments as in the plain cell sort."""
+    rng = np.random.default_rng(6)
+    n, C, S = 6000, 29, 3
+    cell = rng.integers(0, C, n).astype(np.int32)
+    sp = rng.integers(0, S, n).astype(np.int32)
+    base = 10.0 ** rng.uniform(0, 4, n)
+    pick = rng.integers(0, 4, n)
+    ref = base[rng.integers(0, n, n)]
+    # exact ties, ties below the key width (2^-40), distinct just above it (2^-30), and free weights
+    w = np.where(pick == 0, ref, np.where(pick == 1, ref * (1 + 2.0 ** -40), np.where(pick == 2,
+                 ref * (1 + 2.0 ** -30), base)))
+    w[:50] = 1.0
+    perm, off = O.bin_particles_weighted(cell, sp, w, C, S)
+    mant, ex = np.frexp(w)
+    frac = np.floor((2.0 * mant - 1.0) * 2.0 ** 32)
+    seg = cell.astype(np.int64) * S + sp
+    want = np.lexsort((np.arange(n), -frac, -ex, seg))
+    np.testing.assert_array_equal(perm, want)
+    p0, off0 = O.bin_particles(cell, sp, C, S)
+    np.testing.assert_array_equal(off, off0)
+
+
 def test_bin_rejects_out_of_range():
     with pytest.raises(ValueError):
         O.bin_particles(np.array([0, 5], np.int32), np.array([0, 0], np.int32), 3, 1)
