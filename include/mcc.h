@@ -112,6 +112,24 @@ int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n
             int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws, size_t ws_bytes,
             mcc_stream stream);
 
+/* Bytes of device workspace mcc_bin_weighted needs (mcc_bin's counters plus 8 bytes per particle). */
+int mcc_bin_weighted_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t* bytes);
+
+/*
+ * mcc_bin_weighted: the cell sort of mcc_bin with every (cell, species) segment stored in the order of the optional
+ * weight sort of Algorithm 1 (the energy-correction pairs run from the heaviest particle down): descending weight,
+ * the weights compared by their IEEE bits truncated to sign, exponent and 32 fraction bits (weights that agree to
+ * 2^-32 relative tie), ties in increasing particle index. In this layout the fused step finds each segment with
+ * distinct truncated weights already in weight order and skips its per-visit sort; any other layout gives the same
+ * results per layout, only with that sort.
+ *   w               [n] device double, the particle weights (positive, finite), in the caller's (unbinned) order
+ *   other arguments as mcc_bin; ws, ws_bytes at least mcc_bin_weighted_workspace_size bytes
+ * Errors as mcc_bin.
+ */
+int mcc_bin_weighted(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, const double* w, int64_t n,
+                     int32_t n_cells, int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws,
+                     size_t ws_bytes, mcc_stream stream);
+
 /*
  * mcc_bin_static: the same cell sort as mcc_bin for callers that cannot allocate device memory at all, such as
  * code running under an allocator that must not grow, inside a host callback or driver-level integration where

@@ -85,6 +85,9 @@ def lib():
         "mcc_destroy": (None, [vp]),
         "mcc_bin_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_bin": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
+        "mcc_bin_weighted_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
+        "mcc_bin_weighted": (C.c_int, [vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t,
+                                       vp]),
         "mcc_gather": (C.c_int, [vp, vp, C.c_int64, C.c_int32, vp, vp]),
         "mcc_bin_static": (C.c_int, [vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp]),
         "mcc_pair": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -214,6 +217,24 @@ def mcc_bin(cell: torch.Tensor, species: torch.Tensor, n_cells: int, n_species: 
     ws = ctx.workspace("bin", nb.value)
     _check(lib().mcc_bin(ctx.handle, _ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
                          _ptr(ws), nb.value, _stream(stream, cell.device)), "mcc_bin")
+    return perm, offsets
+
+
+def mcc_bin_weighted(cell: torch.Tensor, species: torch.Tensor, w: torch.Tensor, n_cells: int, n_species: int,
+                     stream=None):
+    """Cell sort with each segment in descending-weight order (ties by index); outputs as mcc_bin."""
+    ctx = context(cell.device)
+    n = cell.numel()
+    if w.dtype != torch.float64 or w.numel() != n:
+        raise ValueError("w must be float64 with one weight per particle")
+    perm = torch.empty(n, dtype=torch.int32, device=cell.device)
+    offsets = torch.empty(n_cells * n_species + 1, dtype=torch.int64, device=cell.device)
+    nb = C.c_size_t()
+    _check(lib().mcc_bin_weighted_workspace_size(n, n_cells, n_species, C.byref(nb)),
+           "mcc_bin_weighted_workspace_size")
+    ws = ctx.workspace("bin_weighted", nb.value)
+    _check(lib().mcc_bin_weighted(ctx.handle, _ptr(cell), _ptr(species), _ptr(w), n, n_cells, n_species, _ptr(perm),
+                                  _ptr(offsets), _ptr(ws), nb.value, _stream(stream, cell.device)), "mcc_bin_weighted")
     return perm, offsets
 
 

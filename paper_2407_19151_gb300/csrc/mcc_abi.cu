@@ -303,6 +303,27 @@ int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n
                                        S(stream), &ctx->launches));
 }
 
+int mcc_bin_weighted_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t* bytes)
+{
+    if (!bytes || n < 0 || n_cells <= 0 || n_species <= 0) return MCC_ERR_INVALID_ARG;
+    *bytes = mcc::bin_weighted_workspace_bytes(n, (int64_t)n_cells * n_species);
+    return MCC_OK;
+}
+
+int mcc_bin_weighted(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, const double* w, int64_t n,
+                     int32_t n_cells, int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws,
+                     size_t ws_bytes, mcc_stream stream)
+{
+    if (!ctx || n < 0 || n_cells <= 0 || n_species <= 0 || !offsets_out) return MCC_ERR_INVALID_ARG;
+    if (n > 0 && (!cell || !species || !w || !perm_out)) return MCC_ERR_INVALID_ARG;
+    if (n > INT32_MAX) return MCC_ERR_TOO_LARGE;
+    if (!ws || ws_bytes < mcc::bin_weighted_workspace_bytes(n, (int64_t)n_cells * n_species))
+        return MCC_ERR_WORKSPACE;
+    DeviceGuard g(ctx->device);
+    return cuda_status(mcc::launch_bin_weighted(cell, species, w, n, n_cells, n_species, perm_out, offsets_out, ws,
+                                                ctx->dbuf, S(stream), &ctx->launches));
+}
+
 int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
                    int32_t* perm_out, int64_t* offsets_out, mcc_stream stream)
 {

@@ -20,6 +20,7 @@ namespace {
 constexpr int kBinThreads = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kSegCap = 12288;  // indices sorted in shared memory per segment; larger segments sort in place
+constexpr int kSegCapW = 4096;  // weight-order keys sorted in shared memory per segment; larger ones in the workspace
 
 __global__ void k_hist(const int32_t* __restrict__ cell, const int32_t* __restrict__ species, int64_t n,
                        int32_t n_cells, int32_t S, int32_t* __restrict__ counts, int32_t* status)
@@ -97,6 +98,32 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort(const int64_t* __restri
     }
 }
 
+// Weight order of every segment (run after k_segsort, so a segment's entries are in increasing particle index):
+// keys = weight_key(w, rank) (descending weight truncated to 32 fraction bits, ties by rank = by index), sorted, then
+// each slot takes the index its key's rank points to. keys: [n] workspace, holds the keys of large segments and
+// the reordered indices before they are copied back.
+__global__ void __launch_bounds__(kBinThreads) k_segsort_w(const int64_t* __restrict__ offsets, int64_t nk,
+                                                           const double* __restrict__ w, int32_t* __restrict__ perm,
+                                                           uint64_t* __restrict__ keys)
+{
+    __shared__ uint64_t buf[kSegCapW];
+    for (int64_t seg = blockIdx.x; seg < nk; seg += gridDim.x) {
+        const int64_t b = offsets[seg];
+        const int n = (int)(offsets[seg + 1] - b);
+        if (n < 2) continue;
+        uint64_t* k = n <= kSegCapW ? buf : keys + b;
+        for (int i = threadIdx.x; i < n; i += kBinThreads) k[i] = weight_key(w[perm[b + i]], (uint32_t)i);
+        __syncthreads();
+        block_sort_u64(k, n);
+        // each thread reads only its own slot of k before writing that slot of keys
+        for (int i = threadIdx.x; i < n; i += kBinThreads)
+            keys[b + i] = (uint64_t)(uint32_t)perm[b + (int)(k[i] & kPermMask)];
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += kBinThreads) perm[b + i] = (int32_t)(uint32_t)keys[b + i];
+        __syncthreads();
+    }
+}
+
 template <class T>
 __global__ void k_gather(const T* __restrict__ in, const int32_t* __restrict__ perm, int64_t n, T* __restrict__ out)
 {
@@ -141,6 +168,25 @@ cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, i
         k_segsort<<<gs, kBinThreads, 0, st>>>(offsets, nk, perm);
         *launches += 3;
     }
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+size_t bin_weighted_workspace_bytes(int64_t n, int64_t n_keys)
+{
+    return bin_workspace_bytes(n, n_keys) + (((size_t)n * sizeof(uint64_t) + 255) & ~(size_t)255);
+}
+
+cudaError_t launch_bin_weighted(const int32_t* cell, const int32_t* species, const double* w, int64_t n,
+                                int32_t n_cells, int32_t n_species, int32_t* perm, int64_t* offsets, void* ws,
+                                int32_t* status, cudaStream_t st, int64_t* launches)
+{
+    const int64_t nk = (int64_t)n_cells * n_species;
+    cudaError_t e = launch_bin(cell, species, n, n_cells, n_species, perm, offsets, ws, status, st, launches);
+    if (e != cudaSuccess || n == 0) return e;
+    uint64_t* keys = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + bin_workspace_bytes(n, nk));
+    const int gs = grid_for(nk * kBinThreads, kBinThreads);
+    k_segsort_w<<<gs, kBinThreads, 0, st>>>(offsets, nk, w, perm, keys);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -77,6 +77,10 @@ size_t cell_kernel_static_smem(bool f32, bool rel, int mode);
 cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
                        int32_t* perm, int64_t* offsets, void* ws, int32_t* status, cudaStream_t st, int64_t* launches);
 size_t bin_workspace_bytes(int64_t n, int64_t n_keys);
+cudaError_t launch_bin_weighted(const int32_t* cell, const int32_t* species, const double* w, int64_t n,
+                                int32_t n_cells, int32_t n_species, int32_t* perm, int64_t* offsets, void* ws,
+                                int32_t* status, cudaStream_t st, int64_t* launches);
+size_t bin_weighted_workspace_bytes(int64_t n, int64_t n_keys);
 cudaError_t launch_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
                               int32_t n_species, int32_t* perm, int64_t* offsets, cudaStream_t st);
 int64_t static_bin_max_keys();

@@ -53,6 +53,31 @@ def test_bin_bit_exact(mcc, n, C, S):
     np.testing.assert_array_equal(perm.cpu().numpy(), rperm)
 
 
+@pytest.mark.parametrize("n,C,S", [(0, 4, 2), (1, 1, 1), (1000, 7, 3), (200_000, 4096, 2), (30_000, 3, 1)])
+def test_bin_weighted_bit_exact(mcc, n, C, S):
+    """Weight-ordered segments: exact ties, ties below the key width, distinct weights just above it; one case
+    holds a segment of ~30k particles (keys sorted in the workspace instead of shared memory)."""
+    import torch
+    rng = np.random.default_rng(n + C + 1)
+    if n == 30_000:
+        cell = np.zeros(n, np.int32)
+        cell[::1000] = 2
+    else:
+        cell = rng.integers(0, C, n).astype(np.int32)
+    sp = rng.integers(0, S, n).astype(np.int32)
+    base = 10.0 ** rng.uniform(0, 4, n)
+    ref = base[rng.integers(0, max(n, 1), n)] if n else base
+    pick = rng.integers(0, 4, n)
+    w = np.where(pick == 0, ref, np.where(pick == 1, ref * (1 + 2.0 ** -40),
+                                          np.where(pick == 2, ref * (1 + 2.0 ** -30), base)))
+    perm, off = mcc.mcc_bin_weighted(torch.from_numpy(cell).cuda(), torch.from_numpy(sp).cuda(),
+                                     torch.from_numpy(np.ascontiguousarray(w)).cuda(), C, S)
+    mcc.sync_status(0)
+    rperm, roff = O.bin_particles_weighted(cell, sp, w, C, S)
+    np.testing.assert_array_equal(off.cpu().numpy(), roff)
+    np.testing.assert_array_equal(perm.cpu().numpy(), rperm)
+
+
 def test_bin_out_of_range_latches_bounds(mcc):
     import torch
     cell = torch.tensor([0, 1, 9], dtype=torch.int32, device="cuda")
