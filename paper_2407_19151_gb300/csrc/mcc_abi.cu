@@ -146,6 +146,7 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
             if (!(sp[s].m > 0)) return MCC_ERR_INVALID_ARG;
             a.m[s] = sp[s].m;
             a.m_f[s] = (float)sp[s].m;
+            a.m_lo[s] = (float)(sp[s].m - (double)a.m_f[s]);
             a.ma[s] = sp[s].m;
             a.ma_f[s] = (float)sp[s].m;
         }

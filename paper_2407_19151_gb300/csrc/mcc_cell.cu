@@ -92,7 +92,7 @@ struct Shared {
     int cell;
     int fail;
     alignas(16) unsigned char red_raw[8 * kThreads * 8];  // block_sum partials (8 quantities x 8 bytes)
-    double red[8];
+    alignas(8) unsigned char red[8 * 8];                  // block_sum results (Acc<V>, 8 bytes each)
     double scan_d[kWarps + 1];
     float scan_f[kWarps + 1];
     int iscan[kWarps + 1];
@@ -100,9 +100,116 @@ struct Shared {
     double B[3];
     float Bf[3];
     double D[2];
-    double W1[kMaxSpecies];  // per species sum of w over the cell (static for the visit)
-    double W2[kMaxSpecies];  // per species sum of w^2
+    float Df[2];
+    alignas(8) unsigned char W1[8 * kMaxSpecies];  // per species sum of w over the cell (Acc<V>, fixed for the visit)
+    alignas(8) unsigned char W2[8 * kMaxSpecies];  // per species sum of w^2
 };
+
+template <class V>
+__device__ __forceinline__ Acc<V>* acc_at(unsigned char* p)
+{
+    return reinterpret_cast<Acc<V>*>(p);
+}
+
+// Per-interaction coefficients, computed by one thread from the block sums. FP64 path: in double. Mixed path: in
+// float-float (the float pipe; the FP64 pipe of this part is a small fraction of the float rate).
+// Eq. vp_pm: B = sum_s m_s sum w (v_ps - v_bs) / sum_s m_s sum w^2 over the interaction's species (one side intra).
+__device__ __forceinline__ void shift_coef(const StepArgs& A, const InterConst& ic, bool intra,
+                                           const Acc<double>* r, const Acc<double>* W2, Shared& sh)
+{
+    const double ma = A.m[ic.a], mb = A.m[ic.b];
+    const double Sw = ma * W2[ic.a].x + (intra ? 0.0 : mb * W2[ic.b].x);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double S = ma * r[d].x + (intra ? 0.0 : mb * r[3 + d].x);
+        sh.B[d] = S / Sw;
+        sh.Bf[d] = (float)sh.B[d];
+    }
+}
+__device__ __forceinline__ void shift_coef(const StepArgs& A, const InterConst& ic, bool intra,
+                                           const Acc<float>* r, const Acc<float>* W2, Shared& sh)
+{
+    const ff ma = {A.m_f[ic.a], A.m_lo[ic.a]}, mb = {A.m_f[ic.b], A.m_lo[ic.b]};
+    ff Sw = ff_mul(ma, W2[ic.a].x);
+    if (!intra) Sw = ff_add(Sw, ff_mul(mb, W2[ic.b].x));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ff S = ff_mul(ma, r[d].x);
+        if (!intra) S = ff_add(S, ff_mul(mb, r[3 + d].x));
+        sh.Bf[d] = ff_div(S, Sw).hi;
+    }
+}
+
+// Eq. Econs / Eq. DeltaEs: Delta E of the interaction and its split between the species in proportion to mean
+// weight times post-shift energy; r = {dE_a, E_a, dE_b, E_b} (halves and masses applied here), W1 = sums of w.
+// A species with fewer than two particles cannot take a share; no eligible species with Delta E != 0 fails.
+// |Delta E_s| at or below 2^-47 of species s's post-shift kinetic energy counts as zero (rounding noise).
+__device__ __forceinline__ void partition_coef(const StepArgs& A, const InterConst& ic, bool intra, int na, int nb,
+                                               const Acc<double>* r, const Acc<double>* W1, Shared& sh)
+{
+    const double ma = A.m[ic.a], mb = A.m[ic.b];
+    const double dE = ma * r[0].x + (intra ? 0.0 : mb * r[2].x);
+    double D0 = dE, D1 = 0.0;
+    int fail = 0;
+    if (!intra) {
+        const bool can0 = na >= 2, can1 = nb >= 2;
+        if (can0 && can1) {
+            const double wa = W1[ic.a].x / (double)na * (ma * r[1].x);
+            const double wb = W1[ic.b].x / (double)nb * (mb * r[3].x);
+            const double den = wa + wb;
+            if (den > 0.0) {
+                D0 = wa / den * dE;
+                D1 = dE - D0;
+            } else if (dE != 0.0) {
+                fail = 1;
+            }
+        } else if (can0) {
+            D0 = dE;
+        } else if (can1) {
+            D0 = 0.0;
+            D1 = dE;
+        } else if (dE != 0.0) {
+            fail = 1;
+        }
+    }
+    sh.D[0] = fabs(D0) <= 0x1p-47 * (ma * r[1].x) ? 0.0 : D0;
+    sh.D[1] = fabs(D1) <= 0x1p-47 * (intra ? 0.0 : mb * r[3].x) ? 0.0 : D1;
+    sh.fail = fail;
+}
+__device__ __forceinline__ void partition_coef(const StepArgs& A, const InterConst& ic, bool intra, int na, int nb,
+                                               const Acc<float>* r, const Acc<float>* W1, Shared& sh)
+{
+    const ff ma = {A.m_f[ic.a], A.m_lo[ic.a]}, mb = {A.m_f[ic.b], A.m_lo[ic.b]};
+    const ff Ea = ff_mul(ma, r[1].x), Eb = ff_mul(mb, r[3].x);
+    ff dE = ff_mul(ma, r[0].x);
+    if (!intra) dE = ff_add(dE, ff_mul(mb, r[2].x));
+    ff D0 = dE, D1 = {0.f, 0.f};
+    int fail = 0;
+    if (!intra) {
+        const bool can0 = na >= 2, can1 = nb >= 2;
+        if (can0 && can1) {
+            const ff wa = ff_mul(ff_div(W1[ic.a].x, {(float)na, 0.f}), Ea);
+            const ff wb = ff_mul(ff_div(W1[ic.b].x, {(float)nb, 0.f}), Eb);
+            const ff den = ff_add(wa, wb);
+            if (den.hi > 0.f) {
+                D0 = ff_mul(ff_div(wa, den), dE);
+                D1 = ff_sub(dE, D0);
+            } else if (dE.hi != 0.f) {
+                fail = 1;
+            }
+        } else if (can0) {
+            D0 = dE;
+        } else if (can1) {
+            D0 = {0.f, 0.f};
+            D1 = dE;
+        } else if (dE.hi != 0.f) {
+            fail = 1;
+        }
+    }
+    sh.Df[0] = fabsf(D0.hi) <= 0x1p-47f * Ea.hi ? 0.f : D0.hi;
+    sh.Df[1] = fabsf(D1.hi) <= 0x1p-47f * (intra ? 0.f : Eb.hi) ? 0.f : D1.hi;
+    sh.fail = fail;
+}
 
 constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp in registers
 
@@ -472,18 +579,8 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                     add_weighted_change(mom[side * 3 + d], t, i, t.v[d * cap + i], t.vb[d * cap + i]);
             }
         }
-        block_sum<V, 6>(mom, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
-        if (threadIdx.x == 0) {
-            const double* r = sh.red;
-            const double ma = A.m[ic.a], mb = A.m[ic.b];
-            const double Sw = ma * sh.W2[ic.a] + (intra ? 0.0 : mb * sh.W2[ic.b]);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double S = ma * r[d] + (intra ? 0.0 : mb * r[3 + d]);
-                sh.B[d] = S / Sw;
-                sh.Bf[d] = (float)sh.B[d];
-            }
-        }
+        block_sum<V, 6>(mom, acc_at<V>(sh.red_raw), acc_at<V>(sh.red));
+        if (threadIdx.x == 0) shift_coef(A, ic, intra, acc_at<V>(sh.red), acc_at<V>(sh.W2), sh);
         __syncthreads();
     }
 
@@ -519,39 +616,8 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 }
             }
         }
-        block_sum<V, 4>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
-        if (threadIdx.x == 0) {
-            const double* r = sh.red;
-            const double ma = A.m[ic.a], mb = A.m[ic.b];
-            const double dE = ma * r[0] + (intra ? 0.0 : mb * r[2]);
-            double D0 = dE, D1 = 0.0;
-            int fail = 0;
-            if (!intra) {
-                const bool can0 = na >= 2, can1 = nb >= 2;
-                if (can0 && can1) {
-                    const double wa = sh.W1[ic.a] / (double)na * (ma * r[1]);
-                    const double wb = sh.W1[ic.b] / (double)nb * (mb * r[3]);
-                    const double den = wa + wb;
-                    if (den > 0.0) {
-                        D0 = wa / den * dE;
-                        D1 = dE - D0;
-                    } else if (dE != 0.0) {
-                        fail = 1;
-                    }
-                } else if (can0) {
-                    D0 = dE;
-                } else if (can1) {
-                    D0 = 0.0;
-                    D1 = dE;
-                } else if (dE != 0.0) {
-                    fail = 1;
-                }
-            }
-            // |Delta E_s| at or below 64 ulps (double) of species s's post-shift kinetic energy counts as zero
-            sh.D[0] = fabs(D0) <= 0x1p-47 * (ma * r[1]) ? 0.0 : D0;
-            sh.D[1] = fabs(D1) <= 0x1p-47 * (intra ? 0.0 : mb * r[3]) ? 0.0 : D1;
-            sh.fail = fail;
-        }
+        block_sum<V, 4>(acc, acc_at<V>(sh.red_raw), acc_at<V>(sh.red));
+        if (threadIdx.x == 0) partition_coef(A, ic, intra, na, nb, acc_at<V>(sh.red), acc_at<V>(sh.W1), sh);
         __syncthreads();
     }
 
@@ -559,8 +625,8 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
     int used = 0;
     for (int side = 0; side < nside; ++side) {
         if (sh.fail) break;
-        const double D = sh.D[side];
-        if (D == 0.0) continue;
+        const V D = pick<V>(sh.D[side], sh.Df[side]);
+        if (D == (V)0) continue;
         const int s0 = side ? b0 : a0, ns = side ? nb : na;
         const int spc = side ? ic.b : ic.a;
         const V ms = pick<V>(A.m[spc], A.m_f[spc]);
@@ -571,8 +637,8 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
         if (mode == 2) tie_order<V>(A, t, cs, s0, ns);
         const int32_t* order = (mode == 1) ? t.perm : t.rho;
         auto rho = [&](int m) -> int { return mode == 3 ? s0 + m : order[s0 + m]; };
-        V Dabs = (V)fabs(D);
-        const V sgn = D > 0.0 ? (V)1 : (V)-1;
+        V Dabs = D < (V)0 ? -D : D;
+        const V sgn = D > (V)0 ? (V)1 : (V)-1;
         const V fE = pick<V>(A.fE, A.fE_f);
         bool done = false;
         for (int pass = 0; pass < A.max_corr_passes && !done; ++pass) {
@@ -830,10 +896,10 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
                 const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
                 for (int q = threadIdx.x; q < ns; q += kThreads) add_weight_sums(acc[2 * k], acc[2 * k + 1], t, s0 + q);
             }
-            block_sum<V, 8>(acc, reinterpret_cast<Acc<V>*>(sh.red_raw), sh.red);
+            block_sum<V, 8>(acc, acc_at<V>(sh.red_raw), acc_at<V>(sh.red));
             if (threadIdx.x < 4 && sp0 + (int)threadIdx.x < S) {
-                sh.W1[sp0 + threadIdx.x] = sh.red[2 * threadIdx.x];
-                sh.W2[sp0 + threadIdx.x] = sh.red[2 * threadIdx.x + 1];
+                acc_at<V>(sh.W1)[sp0 + threadIdx.x] = acc_at<V>(sh.red)[2 * threadIdx.x];
+                acc_at<V>(sh.W2)[sp0 + threadIdx.x] = acc_at<V>(sh.red)[2 * threadIdx.x + 1];
             }
         }
         __syncthreads();

@@ -137,6 +137,19 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b)
     return ff_fast_two_sum(p.hi, lo);
 }
 
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+// a / b: float quotient of the high parts, then one correction from the float-float remainder a - q b.
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = ff_sub(a, ff_mul(b, {q1, 0.f}));
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return ff_fast_two_sum(q1, q2);
+}
+
 __device__ __forceinline__ ff ff_from_double(double x)
 {
     const float hi = __double2float_rn(x);
@@ -201,10 +214,10 @@ struct Acc<float> {
 
 // Block-wide sum of M accumulators in a fixed order (reproducible). Each thread parks its M partial sums in shared
 // memory; warp w then reduces quantities w, w + kWarps, ... (its lanes add kThreads/32 partials each, then a warp
-// tree). The M sums are left in out[m] (shared) for the caller to read after the final barrier.
+// tree). The M sums are left in out[m] (shared, accumulator type) for the caller to read after the final barrier.
 // scratch: shared, M * kThreads * sizeof(Acc<V>) bytes. Must be called by all threads of the block.
 template <class V, int M>
-__device__ __forceinline__ void block_sum(Acc<V> (&a)[M], Acc<V>* scratch, double* out)
+__device__ __forceinline__ void block_sum(Acc<V> (&a)[M], Acc<V>* scratch, Acc<V>* out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -216,7 +229,7 @@ __device__ __forceinline__ void block_sum(Acc<V> (&a)[M], Acc<V>* scratch, doubl
         for (int k = 1; k < kThreads / 32; ++k) s.add(scratch[m * kThreads + lane + 32 * k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s.add(s.shfl_xor(o));
-        if (lane == 0) out[m] = s.value();
+        if (lane == 0) out[m] = s;
     }
     __syncthreads();
 }

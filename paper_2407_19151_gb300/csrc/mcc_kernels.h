@@ -30,6 +30,7 @@ struct StepArgs {
     const double* w;
     double m[kMaxSpecies];
     float m_f[kMaxSpecies];
+    float m_lo[kMaxSpecies];  // m - m_f rounded to float: (m_f, m_lo) is m as float-float
     double ma[kMaxSpecies];  // species masses for the relativistic kinematics
     float ma_f[kMaxSpecies];
     InterConst ic[kMaxInter];
