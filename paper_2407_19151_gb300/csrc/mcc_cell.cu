@@ -39,11 +39,14 @@ template <class V>
 struct Tile {
     uint64_t* keys;  // sort keys of segments too large for one warp's registers
     typename WStore<V>::T* w;
-    V* v;            // [3][cap]
-    V* vb;           // [3][cap] pre-interaction copy
+    V* v;            // [3][vs]
+    V* vb;           // [3][bs] pre-interaction copy
     int32_t* perm;   // random permutation of each species segment (cell-local indices)
     int32_t* rho;    // weight-descending order of each species segment (cell-local indices)
-    int cap;
+    uint32_t* cnt;   // bucket counters of the permutation sort (cnt_cap entries)
+    int cap;         // particles the arrays hold
+    int vs, bs;      // plane strides of v and vb
+    int cnt_cap;
 };
 
 template <class V>
@@ -51,13 +54,52 @@ __device__ __forceinline__ Tile<V> make_tile(unsigned char* base, int cap)
 {
     Tile<V> t;
     t.cap = cap;
+    t.vs = t.bs = cap;
     t.keys = reinterpret_cast<uint64_t*>(base);
     t.w = reinterpret_cast<typename WStore<V>::T*>(base + 8 * (size_t)cap);
     t.v = reinterpret_cast<V*>(base + 16 * (size_t)cap);
     t.vb = t.v + 3 * (size_t)cap;
     t.perm = reinterpret_cast<int32_t*>(base + (16 + 6 * sizeof(V)) * (size_t)cap);
     t.rho = t.perm + cap;
+    t.cnt = reinterpret_cast<uint32_t*>(t.vb);  // vb is free while the permutations are built
+    t.cnt_cap = (int)(3 * sizeof(V) / 4) * cap;
     return t;
+}
+
+// A cell above the on-chip tile runs from its CTA's global slab; the shared-memory tile (smem bytes) is then idle,
+// so the arrays that fit move there, in order of how much they gain: the bucket counters (shared-memory atomics),
+// velocities and weights (random access by pair), sort keys, permutation, weight order, pre-interaction copy.
+// ms = the cell's largest species count (the counters of two sides need at most 2 next_pow2(ms) entries).
+template <class V>
+__device__ __forceinline__ void place_on_chip(Tile<V>& t, unsigned char* smem, size_t bytes, int n, int ms)
+{
+    size_t used = 0;
+    auto take = [&](size_t b) -> unsigned char* {
+        b = (b + 15) & ~(size_t)15;
+        if (used + b > bytes) return nullptr;
+        unsigned char* p = smem + used;
+        used += b;
+        return p;
+    };
+    int bm = 1;
+    while (bm < ms) bm <<= 1;
+    const int ns = (n + 3) & ~3;
+    if (unsigned char* p = take(8 * (size_t)bm)) {
+        t.cnt = reinterpret_cast<uint32_t*>(p);
+        t.cnt_cap = 2 * bm;
+    }
+    if (unsigned char* p = take(3 * sizeof(V) * (size_t)ns)) {
+        t.v = reinterpret_cast<V*>(p);
+        t.vs = ns;
+    }
+    if (unsigned char* p = take(8 * (size_t)ns)) t.w = reinterpret_cast<typename WStore<V>::T*>(p);
+    if (unsigned char* p = take(8 * (size_t)ns)) t.keys = reinterpret_cast<uint64_t*>(p);
+    if (unsigned char* p = take(4 * (size_t)ns)) t.perm = reinterpret_cast<int32_t*>(p);
+    if (unsigned char* p = take(4 * (size_t)ns)) t.rho = reinterpret_cast<int32_t*>(p);
+    if (unsigned char* p = take(3 * sizeof(V) * (size_t)ns)) {
+        t.vb = reinterpret_cast<V*>(p);
+        t.bs = ns;
+    }
 }
 
 __device__ __forceinline__ double wv(const Tile<double>& t, int i) { return t.w[i]; }
@@ -248,12 +290,14 @@ __device__ __forceinline__ void warp_sort_buf(uint64_t* buf, int n)
 // Philox keys (44 random bits above the index). The random bits are uniform, so a counting sort on their top
 // log2(B) bits (B = next power of two >= n buckets) already places almost every key; each bucket holding several
 // keys is finished by an insertion sort on the full key. The result is the sort by full key (keys are distinct).
+// One Philox block gives the keys of two consecutive indices, so each thread draws for a pair. The permutation is
+// stored as cell-local particle indices (segment start included).
 // Scratch: the pre-interaction copy vb (unused until after the permutations) holds the bucket counters.
 template <class V>
 __device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, int c, uint32_t ictr, int nside,
                              int a0, int na, int b0, int nb)
 {
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(t.vb);
+    uint32_t* cnt = t.cnt;
     const int s0v[2] = {a0, b0}, nv[2] = {na, nb};
     int lgB[2] = {0, 0}, Bv[2] = {0, 0};
     for (int side = 0; side < nside; ++side) {
@@ -262,9 +306,15 @@ __device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, in
     }
     const int base1 = Bv[0];
     const int L = Bv[0] + (nside > 1 ? Bv[1] : 0);
-    for (int side = 0; side < nside; ++side)
-        for (int q = threadIdx.x; q < nv[side]; q += kThreads)
-            t.keys[s0v[side] + q] = perm_key(A.rng, c, ictr, side, q);
+    for (int side = 0; side < nside; ++side) {
+        const int s0 = s0v[side], n = nv[side];
+        const uint32_t tag = side ? kTagPermB : kTagPermA;
+        for (int h = threadIdx.x; 2 * h < n; h += kThreads) {
+            const uint4 r = draw(A.rng, (uint32_t)h, (uint32_t)c, ictr, tag);
+            t.keys[s0 + 2 * h] = ((((uint64_t)r.x << 32) | r.y) & ~kPermMask) | (uint64_t)(2 * h);
+            if (2 * h + 1 < n) t.keys[s0 + 2 * h + 1] = ((((uint64_t)r.z << 32) | r.w) & ~kPermMask) | (uint64_t)(2 * h + 1);
+        }
+    }
     for (int b = threadIdx.x; b < L; b += kThreads) cnt[b] = 0;
     __syncthreads();
     for (int side = 0; side < nside; ++side) {
@@ -292,16 +342,16 @@ __device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, in
     }
     __syncthreads();
     for (int side = 0; side < nside; ++side) {
-        const int base = side ? base1 : 0, off = side ? na : 0;
+        const int base = side ? base1 : 0, off = side ? na : 0, s0 = s0v[side];
         for (int q = threadIdx.x; q < nv[side]; q += kThreads) {
-            const uint64_t k = t.keys[s0v[side] + q];
+            const uint64_t k = t.keys[s0 + q];
             const int b = lgB[side] ? (int)(k >> (64 - lgB[side])) : 0;
             const int pos = (int)atomicAdd(&cnt[base + b], 1u) - off;
-            t.perm[s0v[side] + pos] = q;
+            t.perm[s0 + pos] = s0 + q;
         }
     }
     __syncthreads();
-    // cnt[b] now holds the end of bucket b: finish buckets with several keys, then store cell-local indices
+    // cnt[b] now holds the end of bucket b: finish buckets with several keys
     for (int side = 0; side < nside; ++side) {
         const int base = side ? base1 : 0, off = side ? na : 0, s0 = s0v[side];
         for (int b = threadIdx.x; b < Bv[side]; b += kThreads) {
@@ -309,9 +359,9 @@ __device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, in
             const int start = b ? (int)cnt[base + b - 1] - off : 0;
             for (int x = start + 1; x < end; ++x) {
                 const int v = t.perm[s0 + x];
-                const uint64_t kv = t.keys[s0 + v];
+                const uint64_t kv = t.keys[v];
                 int y = x - 1;
-                while (y >= start && t.keys[s0 + t.perm[s0 + y]] > kv) {
+                while (y >= start && t.keys[t.perm[s0 + y]] > kv) {
                     t.perm[s0 + y + 1] = t.perm[s0 + y];
                     --y;
                 }
@@ -319,9 +369,6 @@ __device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, in
             }
         }
     }
-    __syncthreads();
-    for (int side = 0; side < nside; ++side)
-        for (int q = threadIdx.x; q < nv[side]; q += kThreads) t.perm[s0v[side] + q] += s0v[side];
     __syncthreads();
 }
 
@@ -333,9 +380,10 @@ template <>
 __device__ __forceinline__ float* scan_scratch<float>(Shared& sh) { return sh.scan_f; }
 
 // k-th Takizuka-Abe pair of the interaction (cell-local indices). See mcc_pair in mcc.h for the rule.
+// pm = p mod N_min (inter only; the callers know it without a division).
 template <class V>
-__device__ __forceinline__ void pair_at(const Tile<V>& t, bool intra, int na, int nb, int a0, int b0, int p, int& i,
-                                        int& j, uint8_t& f)
+__device__ __forceinline__ void pair_at(const Tile<V>& t, bool intra, int na, int nb, int a0, int b0, int p, int pm,
+                                        int& i, int& j, uint8_t& f)
 {
     f = 0;
     if (intra) {
@@ -356,9 +404,9 @@ __device__ __forceinline__ void pair_at(const Tile<V>& t, bool intra, int na, in
     }
     if (na >= nb) {
         i = t.perm[a0 + p];
-        j = t.perm[b0 + p % nb];
+        j = t.perm[b0 + pm];
     } else {
-        i = t.perm[a0 + p % na];
+        i = t.perm[a0 + pm];
         j = t.perm[b0 + p];
     }
 }
@@ -454,9 +502,8 @@ template <class V, bool REL>
 __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t, int c, int64_t cs, uint32_t ictr,
                                              const InterConst& ic, int p, int i, int j, uint8_t f, int nmin)
 {
-    const int cap = t.cap;
-    V vi[3] = {t.v[i], t.v[cap + i], t.v[2 * cap + i]};
-    V vj[3] = {t.v[j], t.v[cap + j], t.v[2 * cap + j]};
+    V vi[3] = {t.v[i], t.v[t.vs + i], t.v[2 * t.vs + i]};
+    V vj[3] = {t.v[j], t.v[t.vs + j], t.v[2 * t.vs + j]};
     const V wi = wv(t, i), wj = wv(t, j);
     const V wmax = wi > wj ? wi : wj;
     const uint4 r = draw(A.rng, (uint32_t)p, (uint32_t)c, ictr, kTagScat);
@@ -516,11 +563,11 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
     }
     if (upd_i) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) t.v[d * cap + i] = vi[d] + dvi[d];
+        for (int d = 0; d < 3; ++d) t.v[d * t.vs + i] = vi[d] + dvi[d];
     }
     if (upd_j) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) t.v[d * cap + j] = vj[d] + dvj[d];
+        for (int d = 0; d < 3; ++d) t.v[d * t.vs + j] = vj[d] + dvj[d];
     }
 }
 
@@ -561,7 +608,6 @@ template <class V, bool REL, int MODE>
 __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int c, int64_t cs,
                                     const InterConst& ic, bool intra, int a0, int na, int b0, int nb)
 {
-    const int cap = t.cap;
     const int nside = intra ? 1 : 2;
     const V cc = pick<V>(A.c, A.c_f);
 
@@ -576,7 +622,7 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 const int i = s0 + q;
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
-                    add_weighted_change(mom[side * 3 + d], t, i, t.v[d * cap + i], t.vb[d * cap + i]);
+                    add_weighted_change(mom[side * 3 + d], t, i, t.v[d * t.vs + i], t.vb[d * t.bs + i]);
             }
         }
         block_sum<V, 6>(mom, acc_at<V>(sh.red_raw), acc_at<V>(sh.red));
@@ -598,9 +644,9 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 V dd = 0, v2 = 0, b2 = 0;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    const V x = t.v[d * cap + i] - pick<V>(sh.B[d], sh.Bf[d]) * w;  // v_pm = v_ps - B w_p
-                    t.v[d * cap + i] = x;
-                    const V y = t.vb[d * cap + i];
+                    const V x = t.v[d * t.vs + i] - pick<V>(sh.B[d], sh.Bf[d]) * w;  // v_pm = v_ps - B w_p
+                    t.v[d * t.vs + i] = x;
+                    const V y = t.vb[d * t.bs + i];
                     dd += (x - y) * (x + y);
                     v2 += x * x;
                     b2 += y * y;
@@ -655,8 +701,8 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                     j = rho(o + 2 * m + 1);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        v1[d] = t.v[d * cap + i];
-                        v2[d] = t.v[d * cap + j];
+                        v1[d] = t.v[d * t.vs + i];
+                        v2[d] = t.v[d * t.vs + j];
                     }
                     m1 = ms * wv(t, i);
                     m2 = ms * wv(t, j);
@@ -689,8 +735,8 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                     }
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        t.v[d * cap + i] = v1[d];
-                        t.v[d * cap + j] = v2[d];
+                        t.v[d * t.vs + i] = v1[d];
+                        t.v[d * t.vs + j] = v2[d];
                     }
                     ++used;
                 }
@@ -712,7 +758,7 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 for (int q = threadIdx.x; q < ns; q += kThreads) {
                     const int i = s0 + q;
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) t.v[d * cap + i] = t.vb[d * cap + i];
+                    for (int d = 0; d < 3; ++d) t.v[d * t.vs + i] = t.vb[d * t.bs + i];
                 }
             }
         }
@@ -739,7 +785,6 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
     const int a0 = sh.off[a], na = sh.off[a + 1] - a0;
     const int b0 = sh.off[b], nb = sh.off[b + 1] - b0;
     const uint32_t ictr = (uint32_t)(A.inter_base + k);
-    const int cap = t.cap;
     const bool active = intra ? (na >= 2) : (na > 0 && nb > 0);
     if (!active) {
         if (MODE == kCorrect && threadIdx.x == 0) {
@@ -756,7 +801,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
         for (int p = threadIdx.x; p < npairs; p += kThreads) {
             int i, j;
             uint8_t f;
-            pair_at(t, intra, na, nb, a0, b0, p, i, j, f);
+            pair_at(t, intra, na, nb, a0, b0, p, intra ? 0 : p % nmin, i, j, f);
             A.pair_i[cs + p] = (int32_t)(cs + i);
             A.pair_j[cs + p] = (int32_t)(cs + j);
             A.pair_flags[cs + p] = f;
@@ -773,10 +818,10 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (MODE == kCorrect) {
-                    t.vb[d * cap + i] = gb[d * A.n_total + cs + i];
+                    t.vb[d * t.bs + i] = gb[d * A.n_total + cs + i];
                 } else {
-                    const V x = t.v[d * cap + i];
-                    t.vb[d * cap + i] = x;
+                    const V x = t.v[d * t.vs + i];
+                    t.vb[d * t.bs + i] = x;
                     if (MODE == kScatter) gb[d * A.n_total + cs + i] = x;
                 }
             }
@@ -784,13 +829,13 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
     }
     __syncthreads();
     if (MODE == kFused || MODE == kScatter) {
-        auto get = [&](int p, int& i, int& j, uint8_t& f) {
+        auto get = [&](int p, int pm, int& i, int& j, uint8_t& f) {
             if (MODE == kScatter) {
                 i = (int)(A.pair_i[cs + p] - cs);
                 j = (int)(A.pair_j[cs + p] - cs);
                 f = A.pair_flags[cs + p];
             } else {
-                pair_at(t, intra, na, nb, a0, b0, p, i, j, f);
+                pair_at(t, intra, na, nb, a0, b0, p, pm, i, j, f);
             }
         };
         // Intra: one round; an odd count starts with the triplet (pairs 0..2 share particles), run in order by thread
@@ -804,7 +849,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
             while (p < r1) {
                 int i, j;
                 uint8_t f;
-                get(p, i, j, f);
+                get(p, p - r0, i, j, f);
                 scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
                 p = (p + 1 < lead) ? p + 1 : (p < lead ? lead + (int)threadIdx.x : p + kThreads);
             }
@@ -865,20 +910,25 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
     } else if (A.slab != nullptr && n <= A.slab_cap) {
         t = make_tile<V>(reinterpret_cast<unsigned char*>(A.slab) + (size_t)blockIdx.x * (size_t)A.slab_stride,
                          A.slab_cap);
+        int ms = 0;
+        for (int sp = 0; sp < S; ++sp) {
+            const int k = (int)(A.offsets[(int64_t)c * S + sp + 1] - A.offsets[(int64_t)c * S + sp]);
+            ms = k > ms ? k : ms;
+        }
+        place_on_chip<V>(t, dyn, (size_t)A.cap * tile_bytes_per_particle(sizeof(V) == 4), n, ms);
     } else {
         if (threadIdx.x == 0) latch(A.status, kErrBounds);
         return;
     }
     if ((int)threadIdx.x <= S) sh.off[threadIdx.x] = (int)(A.offsets[(int64_t)c * S + threadIdx.x] - cs);
-    const int cap = t.cap;
     V* gx = reinterpret_cast<V*>(A.vx);
     V* gy = reinterpret_cast<V*>(A.vy);
     V* gz = reinterpret_cast<V*>(A.vz);
     if (MODE != kPair) {
         for (int i = threadIdx.x; i < n; i += kThreads) {
             t.v[i] = gx[cs + i];
-            t.v[cap + i] = gy[cs + i];
-            t.v[2 * cap + i] = gz[cs + i];
+            t.v[t.vs + i] = gy[cs + i];
+            t.v[2 * t.vs + i] = gz[cs + i];
             w_store(t, i, A.w[cs + i]);
         }
     }
@@ -909,8 +959,8 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
     if (MODE != kPair) {
         for (int i = threadIdx.x; i < n; i += kThreads) {
             gx[cs + i] = t.v[i];
-            gy[cs + i] = t.v[cap + i];
-            gz[cs + i] = t.v[2 * cap + i];
+            gy[cs + i] = t.v[t.vs + i];
+            gz[cs + i] = t.v[2 * t.vs + i];
         }
     }
 }

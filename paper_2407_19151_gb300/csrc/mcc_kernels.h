@@ -63,7 +63,7 @@ struct StepArgs {
 };
 
 // Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation, weight order).
-inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
+__host__ __device__ inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
 
 // N97 table: (f, h df/dx) at kN97Nodes + 1 nodes, computed on the host in double.
 void n97_table(double* f, double* dh);
