@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=1 << 18, help="cells of the three-species workload")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--tile-cap", type=int, default=None,
+                    help="particles per cell staged in shared memory (0: automatic); default: the autotuner's choice")
     ap.add_argument("--layout", default="weight_ordered", choices=["weight_ordered", "generated"],
                     help="particle order within each (cell, species) segment: by descending weight, as mcc_bin_weighted "
                          "stores it, or as generated")
@@ -212,7 +214,11 @@ def run_ours(args):
                            corr_pairs=corr, fail_count=fail)
 
     stream = torch.cuda.current_stream(dev)
-    tile = mcc.autotune_tile_cap(*v, w, off, C, S, species, wl.lnL, params, max_cell)
+    if args.tile_cap is None:
+        tile = mcc.autotune_tile_cap(*v, w, off, C, S, species, wl.lnL, params, max_cell)
+    else:
+        tile = args.tile_cap
+        ctx.set_tile_cap(tile)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(dev)
