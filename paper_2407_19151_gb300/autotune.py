@@ -12,7 +12,7 @@ import torch
 from . import _binding as B
 
 _CACHE: dict[tuple, int] = {}
-CANDIDATES = (0, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
+CANDIDATES = (0, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
 
 
 def autotune_tile_cap(vx, vy, vz, w, offsets, n_cells: int, n_species: int, species, lnL, params: B.Params,
