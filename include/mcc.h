@@ -94,6 +94,33 @@ typedef struct {
 int mcc_create(mcc_ctx** ctx, int device);
 void mcc_destroy(mcc_ctx* ctx);
 
+/* Bytes of device workspace mcc_adjoint needs for n_cells cells of at most max_cell particles. */
+int mcc_adjoint_workspace_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, int32_t max_corr_passes,
+                               size_t* bytes);
+
+/*
+ * mcc_adjoint: one interaction (sa, sb) of a step, recomputed from its input state, and optionally its pathwise
+ * adjoint. Every random draw and discrete decision is held fixed (Philox draws, permutations and TA77 pairs, the
+ * heavier particle's accept test, the weight order, the energy-correction passes and the crossing pair); through the
+ * smooth rest of the interaction (Sec. 3.2 s and angle, Eq. vp_pm, Eq. Econs, Eq. DeltaEs, Eqs. vp1/vp2_inelastic,
+ * U_inelastic; the Sec. 5.2 rollback) it maps dL/dv after the interaction to dL/dv before it and adds dL/dw and
+ * dL/dlnL_ab. Non-relativistic, FP64 (P->prec == MCC_F64) only.
+ *   P               state BEFORE the interaction (device, binned; read only)
+ *   inter, p        the interaction's index in the step and the step's parameters, as for mcc_scatter
+ *   max_cell        largest cell (particles); larger cells latch MCC_ERR_BOUNDS
+ *   v*_out          [n] device: the state after the interaction (all three or none; untouched particles copied)
+ *   gv*             [n] device, in place: in dL/dv after, out dL/dv before (all of gv*, gw, glnL or none)
+ *   gw              [n] device: dL/dw accumulated (+=)
+ *   glnL            device, one double: dL/dlnL_ab accumulated (+=, atomically over cells)
+ *   ws, ws_bytes    at least mcc_adjoint_workspace_size bytes
+ * The recomputed forward equals mcc_scatter followed by mcc_correct for the same inputs (energy passes run in order).
+ * Tape overflow latches MCC_ERR_TOO_LARGE.
+ */
+int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells, int32_t n_species,
+                const mcc_species* sp, const double* lnL, int32_t sa, int32_t sb, int32_t inter, const mcc_params* p,
+                int32_t max_cell, double* vx_out, double* vy_out, double* vz_out, double* gvx, double* gvy,
+                double* gvz, double* gw, double* glnL, void* ws, size_t ws_bytes, mcc_stream stream);
+
 /* Bytes of device workspace mcc_bin needs for n particles and n_keys = n_cells * n_species segments. */
 int mcc_bin_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t* bytes);
 

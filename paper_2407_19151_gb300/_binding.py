@@ -85,6 +85,10 @@ def lib():
         "mcc_destroy": (None, [vp]),
         "mcc_bin_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_bin": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
+        "mcc_adjoint_workspace_size": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, P(C.c_size_t)]),
+        "mcc_adjoint": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), P(C.c_double), C.c_int32,
+                                  C.c_int32, C.c_int32, P(_Params), C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                  C.c_size_t, vp]),
         "mcc_bin_weighted_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_bin_weighted": (C.c_int, [vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t,
                                        vp]),
@@ -285,6 +289,29 @@ def mcc_scatter(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, sa, sb
                              _lnL(lnL, n_species), sa, sb, inter, _ptr(pi), _ptr(pj), _ptr(fl), C.byref(cp),
                              _ptr(backup), _stream(stream, vx.device)), "mcc_scatter")
     return backup[:, : vx.numel()]
+
+
+def mcc_adjoint(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, sa, sb, inter, params: Params,
+                max_cell: int, out=None, grad=None, gw=None, glnL=None, stream=None):
+    """One interaction from the state (vx, vy, vz) before it: writes the state after it into ``out`` (three tensors)
+    and/or maps ``grad`` (three tensors, dL/dv after, in place) to dL/dv before, adding dL/dw into ``gw`` and
+    dL/dlnL_ab into ``glnL`` (one-element float64 tensor). FP64, non-relativistic."""
+    ctx = context(vx.device)
+    P = _particles(vx, vy, vz, w)
+    nb = C.c_size_t()
+    _check(lib().mcc_adjoint_workspace_size(ctx.handle, int(n_cells), int(max_cell), int(params.max_corr_passes),
+                                            C.byref(nb)), "mcc_adjoint_workspace_size")
+    ws = ctx.workspace("adjoint", nb.value)
+    o = out if out is not None else (None, None, None)
+    g = grad if grad is not None else (None, None, None)
+    for t in [*(x for x in o if x is not None), *(x for x in g if x is not None), gw, glnL]:
+        if t is not None and (t.dtype != torch.float64 or not t.is_contiguous() or t.device != vx.device):
+            raise TypeError("outputs and gradients must be contiguous float64 tensors on the particles' device")
+    cp = params._c()
+    _check(lib().mcc_adjoint(ctx.handle, C.byref(P), _ptr(offsets), n_cells, n_species, _species(species),
+                             _lnL(lnL, n_species), sa, sb, inter, C.byref(cp), int(max_cell), _ptr(o[0]), _ptr(o[1]),
+                             _ptr(o[2]), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(gw), _ptr(glnL), _ptr(ws), nb.value,
+                             _stream(stream, vx.device)), "mcc_adjoint")
 
 
 def mcc_correct(vx, vy, vz, w, offsets, n_cells, n_species, species, sa, sb, inter, params: Params,

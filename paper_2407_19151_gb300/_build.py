@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu"]
+SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu", "mcc_adjoint.cu"]
 HEADERS = ["mcc_device.cuh", "mcc_kernels.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

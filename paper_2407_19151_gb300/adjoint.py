@@ -1,0 +1,88 @@
+"""Differentiable collision steps: torch.autograd.Function over the fused FP64 step with a hand-written adjoint.
+
+The gradient is pathwise: the random stream and every discrete decision of each step (pairs, accept tests, weight
+order, energy-correction passes and crossing pairs) are held fixed, and the chain rule runs backwards through the
+smooth rest of each interaction in the CUDA kernel behind ``mcc_adjoint``. Gradients flow to the initial velocities,
+the weights and the Coulomb logarithms (the upper-triangle entries lnL[a, b], a <= b, that the interactions use).
+
+Checkpointing: the forward keeps the state at every ``checkpoint_every``-th step; the backward replays each segment
+from its checkpoint (one interaction at a time, storing the state before every interaction of the segment), then
+walks the segment backwards. Memory: checkpoint_every x interactions states of the segment, plus the checkpoints.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+class _CollisionSteps(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vx, vy, vz, w, lnL, cfg):
+        v = [vx.detach().clone(), vy.detach().clone(), vz.detach().clone()]
+        L = lnL.detach().cpu().numpy()
+        ckpts = []
+        for t in range(cfg["n_steps"]):
+            if t % cfg["every"] == 0:
+                ckpts.append([x.clone() for x in v])
+            p = dataclasses.replace(cfg["params"], step=cfg["params"].step + t)
+            B.mcc_step_fused(*v, w.detach(), cfg["offsets"], cfg["n_cells"], cfg["S"], cfg["species"], L, p,
+                             n_steps=1, max_cell=cfg["max_cell"], interactions=cfg["inter"])
+        B.sync_status(vx.device)
+        ctx.save_for_backward(w, lnL)
+        ctx.ckpts = ckpts
+        ctx.cfg = cfg
+        return v[0], v[1], v[2]
+
+    @staticmethod
+    def backward(ctx, gx, gy, gz):
+        w, lnL = ctx.saved_tensors
+        cfg = ctx.cfg
+        w = w.detach()
+        L = lnL.detach().cpu().numpy()
+        dev = w.device
+        g = [(x if x is not None else torch.zeros_like(w)).detach().to(torch.float64).contiguous().clone()
+             for x in (gx, gy, gz)]
+        gw = torch.zeros_like(w)
+        inter = cfg["inter"]
+        glnl = torch.zeros(len(inter), dtype=torch.float64, device=dev)
+        every, n_steps = cfg["every"], cfg["n_steps"]
+        common = (cfg["offsets"], cfg["n_cells"], cfg["S"], cfg["species"], L)
+        for seg in reversed(range(len(ctx.ckpts))):
+            t0, t1 = seg * every, min(seg * every + every, n_steps)
+            v = [x.clone() for x in ctx.ckpts[seg]]
+            tape = []
+            for t in range(t0, t1):
+                p = dataclasses.replace(cfg["params"], step=cfg["params"].step + t)
+                for k, (a, b) in enumerate(inter):
+                    out = [torch.empty_like(x) for x in v]
+                    B.mcc_adjoint(*v, w, *common, a, b, k, p, cfg["max_cell"], out=out)
+                    tape.append((k, a, b, p, v))
+                    v = out
+            for k, a, b, p, vb in reversed(tape):
+                B.mcc_adjoint(*vb, w, *common, a, b, k, p, cfg["max_cell"], grad=g, gw=gw, glnL=glnl[k:k + 1])
+        B.sync_status(dev)
+        gL = torch.zeros(lnL.shape, dtype=torch.float64)
+        gl = glnl.cpu()
+        for k, (a, b) in enumerate(inter):
+            gL[a, b] += gl[k]
+        return g[0], g[1], g[2], gw, gL.to(lnL.device, lnL.dtype), None
+
+
+def collision_steps(vx, vy, vz, w, lnL, offsets, n_cells: int, n_species: int, species, params: B.Params,
+                    n_steps: int, max_cell: int | None = None, checkpoint_every: int = 10, interactions=None):
+    """n_steps FP64 collision steps (non-relativistic), differentiable with respect to vx, vy, vz, w and lnL (a float64
+    tensor of shape (S, S)). Returns the final (vx, vy, vz); the inputs are not modified."""
+    if vx.dtype != torch.float64 or params.relativistic:
+        raise ValueError("the differentiable step is FP64 and non-relativistic")
+    if max_cell is None:
+        max_cell = int((offsets[n_species::n_species] - offsets[:-1:n_species]).max().item()) if n_cells else 0
+    inter = B.default_interactions(n_species) if interactions is None else [tuple(x) for x in interactions]
+    if not torch.is_tensor(lnL):
+        lnL = torch.as_tensor(np.broadcast_to(np.asarray(lnL, dtype=np.float64), (n_species, n_species)).copy())
+    cfg = dict(offsets=offsets, n_cells=int(n_cells), S=int(n_species), species=list(species), params=params,
+               n_steps=int(n_steps), max_cell=int(max_cell), every=max(1, int(checkpoint_every)), inter=inter)
+    return _CollisionSteps.apply(vx, vy, vz, w, lnL, cfg)

@@ -85,6 +85,11 @@ size_t bin_weighted_workspace_bytes(int64_t n, int64_t n_keys);
 cudaError_t launch_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
                               int32_t n_species, int32_t* perm, int64_t* offsets, cudaStream_t st);
 int64_t static_bin_max_keys();
+// Adjoint of one interaction (mcc_adjoint.cu).
+size_t adjoint_slab_bytes(int32_t max_cell, int32_t max_epairs);
+cudaError_t launch_adjoint(const StepArgs& a, double lnL, double* ox, double* oy, double* oz, double* gx, double* gy,
+                           double* gz, double* gw, double* glnL, char* slab, int32_t max_cell, int32_t max_epairs,
+                           int grid, cudaStream_t st);
 cudaError_t launch_gather(const void* in, const int32_t* perm, int64_t n, int elem_bytes, void* out, cudaStream_t st);
 
 }  // namespace mcc

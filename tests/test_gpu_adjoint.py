@@ -1,0 +1,147 @@
+"""GPU parity of the pathwise adjoint (mcc_adjoint, collision_steps) against the oracle: its recomputed forward
+against the oracle step, its gradients against the closed forms that exact momentum and energy conservation fix,
+and against central differences of the oracle step on the same seed."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import gradient as G
+from paper_2407_19151_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcc():
+    import paper_2407_19151_gb300 as m
+    m.build()
+    return m
+
+
+def _tensors(wl):
+    import torch
+    v = [torch.tensor(np.asarray(x, dtype=np.float64), device="cuda") for x in (wl.vx, wl.vy, wl.vz)]
+    w = torch.tensor(wl.w, dtype=torch.float64, device="cuda")
+    off = torch.tensor(wl.offsets, device="cuda")
+    L = torch.tensor(np.asarray(wl.lnL, dtype=np.float64))
+    return v, w, off, L
+
+
+def _case(method, n_cells=3, per_species=12, dt_scale=20):
+    wl = W.differentiable(n_cells=n_cells, per_species=per_species)
+    wl.method = method
+    kw = dict(method=method, dt=wl.dt * dt_scale, fE=wl.fE, seed=wl.seed, step=3)
+    return wl, kw
+
+
+@pytest.mark.parametrize("method", [W.TA77, W.N97])
+def test_adjoint_forward_matches_oracle(mcc, method):
+    import torch
+    wl, kw = _case(method, n_cells=24, per_species=40)
+    v, w, off, _ = _tensors(wl)
+    p = mcc.Params(**kw)
+    sp = list(zip(wl.q.tolist(), wl.m.tolist()))
+    mc = int(wl.counts.sum(1).max())
+    for k, (a, b) in enumerate(mcc.default_interactions(wl.n_species)):
+        out = [torch.empty_like(x) for x in v]
+        mcc.mcc_adjoint(*v, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, a, b, k, p, mc, out=out)
+        v = out
+    mcc.sync_status(0)
+    st = O.State(wl.vx, wl.vy, wl.vz, wl.w, wl.offsets, wl.n_cells, wl.n_species)
+    O.step(st, wl.q, wl.m, wl.lnL, O.Params(**kw))
+    got = np.stack([x.cpu().numpy() for x in v], axis=1)
+    ref = st.v()
+    scale = np.sqrt((ref ** 2).sum(1).mean())
+    assert np.abs(got - ref).max() / scale < 1e-12
+
+
+def _grads(mcc, wl, kw, cot_fn, n_steps=2, every=10):
+    import torch
+    v, w, off, L = _tensors(wl)
+    for x in (*v, w, L):
+        x.requires_grad_(True)
+    sp = list(zip(wl.q.tolist(), wl.m.tolist()))
+    out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, sp, mcc.Params(**kw), n_steps,
+                              checkpoint_every=every)
+    vf = np.stack([x.detach().cpu().numpy() for x in out], axis=1)
+    cot = torch.tensor(cot_fn(vf), device="cuda")
+    loss = sum((cot[:, d] * out[d]).sum() for d in range(3))
+    loss.backward()
+    gv = np.stack([x.grad.cpu().numpy() for x in v], axis=1)
+    return vf, gv, w.grad.cpu().numpy(), L.grad.numpy()
+
+
+@pytest.mark.parametrize("method", [W.TA77, W.N97])
+def test_adjoint_conservation_closed_forms(mcc, method):
+    """Momentum: cot = m w e_x gives dL/dv = m w e_x, dL/dw = m (v0_x - vf_x), dL/dlnL = 0. Energy: cot = m w vf gives
+    dL/dv = m w v0, dL/dw = m (|v0|^2 - |vf|^2)/2, dL/dlnL = 0 (every particle, not a sample)."""
+    wl, kw = _case(method, n_cells=16, per_species=64)
+    sp = wl.species_of_particles()
+    mw = wl.m[sp] * wl.w
+    v0 = np.stack([wl.vx, wl.vy, wl.vz], axis=1)
+
+    def cot_p(vf):
+        c = np.zeros_like(vf)
+        c[:, 0] = mw
+        return c
+
+    vf, gv, gw, gL = _grads(mcc, wl, kw, cot_p)
+    scale = mw * np.maximum(np.abs(v0).max(1), np.abs(vf).max(1))
+    want = np.zeros_like(v0)
+    want[:, 0] = mw
+    assert (np.abs(gv - want).max(1) / mw).max() < 1e-9
+    assert (np.abs(gw - wl.m[sp] * (v0[:, 0] - vf[:, 0])) * wl.w / scale).max() < 1e-9
+    assert np.abs(gL).max() < 1e-9 * np.abs(mw[:, None] * vf).sum()
+
+    vf, gv, gw, gL = _grads(mcc, wl, kw, lambda vf: mw[:, None] * vf)
+    e0 = (v0 ** 2).sum(1)
+    ef = (vf ** 2).sum(1)
+    escale = mw * np.maximum(e0, ef)
+    assert (np.abs(gv - mw[:, None] * v0).max(1) * np.abs(v0).max(1) / escale).max() < 1e-9
+    assert (np.abs(gw - 0.5 * wl.m[sp] * (e0 - ef)) * wl.w / escale).max() < 1e-9
+    assert np.abs(gL).max() < 1e-9 * (mw * ef).sum()
+
+
+@pytest.mark.parametrize("method", [W.TA77, W.N97])
+def test_adjoint_matches_oracle_finite_differences(mcc, method):
+    """A random cotangent: sampled entries of dL/dv, dL/dw and dL/dlnL against central differences of the oracle
+    step (samples whose difference quotients at h and h/2 disagree straddle a decision and are skipped)."""
+    wl, kw = _case(method)
+    rng = np.random.default_rng(11)
+    cot = rng.standard_normal((wl.n, 3))
+    vf, gv, gw, gL = _grads(mcc, wl, kw, lambda vf: cot)
+    v0 = np.stack([wl.vx, wl.vy, wl.vz], axis=1)
+    args = (wl.offsets, wl.n_cells, wl.n_species, wl.q, wl.m, wl.lnL, O.Params(**kw), 2)
+    checked = 0
+    for idx in rng.choice(wl.n, 10, replace=False):
+        idx = int(idx)
+        for d in range(3):
+            g, g2, same = G.fd_derivative(cot, v0, wl.w, *args, ("v", idx, d))
+            tol = 1e-6 * max(abs(g), np.abs(cot).max())
+            if same and abs(g - g2) <= tol:
+                assert abs(gv[idx, d] - g) <= tol, (idx, d, gv[idx, d], g)
+                checked += 1
+        g, g2, same = G.fd_derivative(cot, v0, wl.w, *args, ("w", idx))
+        tol = 1e-6 * max(abs(g), np.abs(cot).max() * np.abs(v0).max() / wl.w[idx])
+        if same and abs(g - g2) <= tol:
+            assert abs(gw[idx] - g) <= tol, (idx, gw[idx], g)
+            checked += 1
+    for a, b in ((0, 0), (0, 1), (1, 1)):
+        g, g2, same = G.fd_derivative(cot, v0, wl.w, *args, ("lnL", a, b))
+        tol = 1e-6 * max(abs(g), 1e-3 * np.abs(cot * v0).sum() / wl.lnL[a, b])
+        if same and abs(g - g2) <= tol:
+            assert abs(gL[a, b] - g) <= tol, (a, b, gL[a, b], g)
+            checked += 1
+    assert checked >= 30
+
+
+def test_adjoint_checkpoint_segments_agree(mcc):
+    """The backward replays each checkpoint segment: segments of 1, 3 and 10 steps give the same gradient."""
+    wl, kw = _case(W.N97, n_cells=8, per_species=32)
+    rng = np.random.default_rng(3)
+    cot = rng.standard_normal((wl.n, 3))
+    res = [_grads(mcc, wl, kw, lambda vf: cot, n_steps=4, every=e) for e in (1, 3, 10)]
+    for r in res[1:]:
+        assert np.allclose(r[1], res[0][1], rtol=1e-9, atol=1e-9 * np.abs(res[0][1]).max())
+        assert np.allclose(r[2], res[0][2], rtol=1e-9, atol=1e-9 * np.abs(res[0][2]).max())
+        assert np.allclose(r[3], res[0][3], rtol=1e-9, atol=1e-9 * np.abs(res[0][3]).max())
