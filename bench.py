@@ -48,6 +48,7 @@ def parse():
                          "stores it, or as generated")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -182,6 +183,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_measure(dev):
+    """Differentiable step (1024 cells x 512 particles, two species of mass ratio 1836, FP64, N97): 50 steps with a
+    checkpoint every 10, gradient of the final per-species temperatures and drifts with respect to the initial
+    velocities, weights and Coulomb logarithms. Forward and backward timed separately with CUDA events."""
+    import torch
+
+    import paper_2407_19151_gb300 as mcc
+    from paper_2407_19151_gb300 import workloads as W
+    wl = W.differentiable(n_cells=1024, per_species=256)
+    n_steps, every = 50, 10
+    v = [torch.tensor(x, dtype=torch.float64, device=dev, requires_grad=True) for x in (wl.vx, wl.vy, wl.vz)]
+    w = torch.tensor(wl.w, dtype=torch.float64, device=dev, requires_grad=True)
+    L = torch.tensor(wl.lnL, dtype=torch.float64, requires_grad=True)
+    off = torch.from_numpy(wl.offsets).to(dev)
+    sp_of = torch.from_numpy(wl.species_of_particles()).to(dev).long()
+    m = torch.tensor(wl.m, dtype=torch.float64, device=dev)[sp_of]
+    species = list(zip(wl.q.tolist(), wl.m.tolist()))
+    params = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
+
+    def temps_drifts(out):
+        loss = 0.0
+        for s in range(wl.n_species):
+            sel = sp_of == s
+            ws = w[sel]
+            V = [torch.sum(ws * x[sel]) / torch.sum(ws) for x in out]
+            T = sum(torch.sum(ws * (x[sel] - Vd) ** 2) for x, Vd in zip(out, V)) * wl.m[s] / (3 * torch.sum(ws))
+            loss = loss + T + sum(V)
+        return loss
+
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, species, params, 2, checkpoint_every=every)
+    temps_drifts(out).backward()  # warm-up (library load, workspaces)
+    for x in (*v, w, L):
+        x.grad = None
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, species, params, n_steps,
+                              checkpoint_every=every)
+    loss = temps_drifts(out)
+    ev[1].record(stream)
+    loss.backward()
+    ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    pairs = wl.pairs_per_step() * n_steps
+    return {"workload": "differentiable, 1024 cells x 512, two species, FP64, N97", "steps": n_steps,
+            "checkpoint_every": every, "forward_ms": f_ms, "backward_ms": b_ms,
+            "pairs_per_s_forward_backward": pairs / ((f_ms + b_ms) * 1e-3),
+            "grad_norms": {"v": float(sum(x.grad.norm() ** 2 for x in v) ** 0.5), "w": float(w.grad.norm()),
+                           "lnL": float(L.grad.norm())}}
+
+
 def run_ours(args):
     import torch
 
@@ -303,6 +357,7 @@ def run_ours(args):
 
     if rank != 0:
         return
+    adj = None if (args.no_adjoint or world > 1) else adjoint_measure(dev)
     cb = None if (args.no_cpu or world > 1) else cpu_baseline(wl)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -324,6 +379,7 @@ def run_ours(args):
         "gpu_launches": args.steps + 1,  # one persistent step kernel per captured step + the cell-order kernel
         "correction_failures": fails,
         "fp64_step": fp64,
+        "adjoint": adj,
         "cpu_baseline": cb,
     }
     print(json.dumps(line), flush=True)
