@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-bin", action="store_true")
     return ap.parse_args()
 
 
@@ -141,7 +142,7 @@ def make_workload(cells: int, rank: int, precision: str, layout: str = "weight_o
     return wl.weight_ordered() if layout == "weight_ordered" else wl
 
 
-def cpu_baseline(wl, budget_s: float = 15.0):
+def cpu_baseline(wl, budget_s: float = 15.0, one_thread: bool = False):
     """The oracle as it stands on the host cores (OpenMP over cells), on the first cells of the same workload:
     grows the sample until a run takes a few seconds, then reports pairs/s."""
     import oracle as O
@@ -163,8 +164,23 @@ def cpu_baseline(wl, budget_s: float = 15.0):
         if dt > budget_s / 3 or spent > budget_s or k >= wl.n_cells:
             break
         k = min(wl.n_cells, int(k * max(2.0, (budget_s / 3) / max(dt, 1e-3))))
-    return {"value": best[0], "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-            "sample": f"one step of the first {best[1]} cells ({best[2]:.1f} s, FP64 C oracle, OpenMP over cells)"}
+    out = {"value": best[0], "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+           "sample": f"one step of the first {best[1]} cells ({best[2]:.1f} s, FP64 C oracle, OpenMP over cells)"}
+    if one_thread:
+        # the same oracle on one host thread, on the first 1024 cells
+        k = min(1024, wl.n_cells)
+        sub = wl.subset(k)
+        st = O.State(sub.vx.astype(np.float64), sub.vy.astype(np.float64), sub.vz.astype(np.float64), sub.w,
+                     sub.offsets, sub.n_cells, sub.n_species)
+        p = O.Params(method=sub.method, dt=sub.dt, dV=sub.dV, eps0=sub.eps0, c=sub.c, fE=sub.fE, seed=sub.seed)
+        O.set_threads(1)
+        t0 = time.perf_counter()
+        O.step(st, sub.q, sub.m, sub.lnL, p, n_steps=1)
+        dt = time.perf_counter() - t0
+        O.set_threads(cores)
+        out["one_thread"] = {"value": sub.pairs_per_step() / dt, "unit": UNIT,
+                             "sample": f"one step of the first {k} cells ({dt:.1f} s, one thread)"}
+    return out
 
 
 def run_reference(args):
@@ -181,6 +197,47 @@ def run_reference(args):
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def bin_measure(wl, dev):
+    """One-time cell sort of the same particles from a shuffled order (row a1, reported apart from the step):
+    mcc_bin (stable by cell and species), mcc_bin_weighted (segments by descending weight) and the gather of
+    vx, vy, vz, w through the permutation; CUDA events, after one untimed call each."""
+    import torch
+
+    import paper_2407_19151_gb300 as mcc
+    rng = np.random.default_rng(7)
+    order = rng.permutation(wl.n)
+    cell = torch.from_numpy(wl.cell_of_particles()[order]).to(dev)
+    species = torch.from_numpy(wl.species_of_particles()[order]).to(dev)
+    w = torch.from_numpy(wl.w[order]).to(dev)
+    v = [torch.from_numpy(np.ascontiguousarray(x[order])).to(dev) for x in (wl.vx, wl.vy, wl.vz)]
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, fn in (("bin", lambda: mcc.mcc_bin(cell, species, wl.n_cells, wl.n_species)),
+                     ("bin_weighted", lambda: mcc.mcc_bin_weighted(cell, species, w, wl.n_cells, wl.n_species))):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        perm, _ = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name + "_ms"] = e0.elapsed_time(e1)
+    mcc.sync_status(dev.index or 0)
+    for x in (*v, w):
+        mcc.mcc_gather(x, perm)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for x in (*v, w):
+        mcc.mcc_gather(x, perm)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    res["gather_ms"] = e0.elapsed_time(e1)
+    res["particles"] = wl.n
+    res["note"] = "one-time cost (positions frozen in the step); the step itself reads the binned arrays"
+    return res
 
 
 def adjoint_measure(dev):
@@ -358,7 +415,8 @@ def run_ours(args):
     if rank != 0:
         return
     adj = None if (args.no_adjoint or world > 1) else adjoint_measure(dev)
-    cb = None if (args.no_cpu or world > 1) else cpu_baseline(wl)
+    binning = None if (args.no_bin or world > 1) else bin_measure(wl, dev)
+    cb = None if (args.no_cpu or world > 1) else cpu_baseline(wl, one_thread=True)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -380,6 +438,7 @@ def run_ours(args):
         "correction_failures": fails,
         "fp64_step": fp64,
         "adjoint": adj,
+        "binning": binning,
         "cpu_baseline": cb,
     }
     print(json.dumps(line), flush=True)

@@ -85,6 +85,7 @@ def lib():
         sig = {
             "orc_philox4x32_10": (None, [u32, u32, u32]),
             "orc_bin": (C.c_int, [i32, i32, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
+            "orc_set_threads": (None, [C.c_int32]),
             "orc_bin_weighted": (C.c_int, [i32, i32, d, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
             "orc_permutation": (C.c_int, [C.c_int64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                           i32]),
@@ -128,6 +129,11 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
     return out
+
+
+def set_threads(n: int):
+    """Host threads used by step() (timing only)."""
+    lib().orc_set_threads(int(n))
 
 
 def bin_particles(cell, species, n_cells: int, n_species: int):

@@ -23,6 +23,10 @@
  */
 #include "mcc_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <math.h>
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -839,4 +843,14 @@ int orc_step(double* vx, double* vy, double* vz, const double* w, const int64_t*
         free(backup);
     }
     return rc;
+}
+
+/* Host threads of the cell loop of orc_step (timing only; the results do not depend on it). */
+void orc_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }

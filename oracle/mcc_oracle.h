@@ -75,6 +75,8 @@ int orc_correct(double* vx, double* vy, double* vz, const double* w, const int64
                 int32_t n_species, const double* m, int32_t sa, int32_t sb, int32_t inter, const orc_params* p,
                 const double* backup, int32_t* corr_pairs, int32_t* fail_flags);
 
+void orc_set_threads(int32_t n);
+
 int orc_step(double* vx, double* vy, double* vz, const double* w, const int64_t* offsets, int32_t n_cells,
              int32_t n_species, const double* q, const double* m, const double* lnL, const int32_t* interactions,
              int32_t n_inter, const orc_params* p, int32_t n_steps, int32_t cell_begin, int32_t cell_end,
