@@ -47,7 +47,7 @@ def parse():
                     help="particle order within each (cell, species) segment: by descending weight, as mcc_bin_weighted "
                          "stores it, or as generated")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=8, help="cell chunks of the host-buffer pipeline")
+    ap.add_argument("--e2e-chunks", type=int, default=4, help="cell chunks of the host-buffer pipeline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-bin", action="store_true")

@@ -19,7 +19,7 @@ from .sharding import shard_cells, shard_view
 
 
 def step_host(vx, vy, vz, w, offsets, n_cells: int, n_species: int, species, lnL, params: B.Params,
-              n_steps: int = 1, max_cell: int | None = None, chunks: int = 8, buffers: int = 2, device=0,
+              n_steps: int = 1, max_cell: int | None = None, chunks: int = 4, buffers: int = 2, device=0,
               interactions=None):
     """Advance the host state (vx, vy, vz: pinned CPU tensors, float32 or float64; w: pinned float64) by n_steps
     in place. offsets: host int64 segment offsets. Returns the per-cell (corr_pairs, fail_count) as host arrays."""
