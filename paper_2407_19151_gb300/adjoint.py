@@ -1,4 +1,4 @@
-"""Differentiable collision steps: torch.autograd.Function over the fused FP64 step with a hand-written adjoint.
+"""Differentiable collision steps: torch.autograd.Function over the fused step with a hand-written adjoint.
 
 The gradient is pathwise: the random stream and every discrete decision of each step (pairs, accept tests, weight
 order, energy-correction passes and crossing pairs) are held fixed, and the chain rule runs backwards through the
@@ -8,6 +8,11 @@ the weights and the Coulomb logarithms (the upper-triangle entries lnL[a, b], a 
 Checkpointing: the forward keeps the state at every ``checkpoint_every``-th step; the backward replays each segment
 from its checkpoint (one interaction at a time, storing the state before every interaction of the segment), then
 walks the segment backwards. Memory: checkpoint_every x interactions states of the segment, plus the checkpoints.
+
+Two variants, chosen by the velocity dtype: float64 runs the FP64 step forward; float32 runs the mixed-precision step
+forward (float velocities, float-float sums) and, in the backward, replays each segment in FP64 from its float
+checkpoint and takes the FP64 adjoint there, returning float32 velocity gradients. The FP32 variant's gradient is the
+FP64 gradient at a trajectory within float rounding of the one its forward took.
 """
 from __future__ import annotations
 
@@ -23,6 +28,7 @@ class _CollisionSteps(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vx, vy, vz, w, lnL, cfg):
         v = [vx.detach().clone(), vy.detach().clone(), vz.detach().clone()]
+        ctx.vdtype = vx.dtype
         L = lnL.detach().cpu().numpy()
         ckpts = []
         for t in range(cfg["n_steps"]):
@@ -53,7 +59,7 @@ class _CollisionSteps(torch.autograd.Function):
         common = (cfg["offsets"], cfg["n_cells"], cfg["S"], cfg["species"], L)
         for seg in reversed(range(len(ctx.ckpts))):
             t0, t1 = seg * every, min(seg * every + every, n_steps)
-            v = [x.clone() for x in ctx.ckpts[seg]]
+            v = [x.to(torch.float64) for x in ctx.ckpts[seg]]
             tape = []
             for t in range(t0, t1):
                 p = dataclasses.replace(cfg["params"], step=cfg["params"].step + t)
@@ -69,15 +75,17 @@ class _CollisionSteps(torch.autograd.Function):
         gl = glnl.cpu()
         for k, (a, b) in enumerate(inter):
             gL[a, b] += gl[k]
-        return g[0], g[1], g[2], gw, gL.to(lnL.device, lnL.dtype), None
+        gv = [x.to(ctx.vdtype) for x in g]
+        return gv[0], gv[1], gv[2], gw, gL.to(lnL.device, lnL.dtype), None
 
 
 def collision_steps(vx, vy, vz, w, lnL, offsets, n_cells: int, n_species: int, species, params: B.Params,
                     n_steps: int, max_cell: int | None = None, checkpoint_every: int = 10, interactions=None):
-    """n_steps FP64 collision steps (non-relativistic), differentiable with respect to vx, vy, vz, w and lnL (a float64
-    tensor of shape (S, S)). Returns the final (vx, vy, vz); the inputs are not modified."""
-    if vx.dtype != torch.float64 or params.relativistic:
-        raise ValueError("the differentiable step is FP64 and non-relativistic")
+    """n_steps collision steps (non-relativistic), differentiable with respect to vx, vy, vz, w (float64) and lnL (a
+    float64 tensor of shape (S, S)). float64 velocities: the FP64 step; float32: the mixed-precision step with the
+    FP64 adjoint replayed from float checkpoints. Returns the final (vx, vy, vz); the inputs are not modified."""
+    if vx.dtype not in (torch.float64, torch.float32) or params.relativistic:
+        raise ValueError("the differentiable step takes float64 or float32 velocities and is non-relativistic")
     if max_cell is None:
         max_cell = int((offsets[n_species::n_species] - offsets[:-1:n_species]).max().item()) if n_cells else 0
     inter = B.default_interactions(n_species) if interactions is None else [tuple(x) for x in interactions]
