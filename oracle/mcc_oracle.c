@@ -402,6 +402,21 @@ typedef struct {
 typedef struct { double* p; int64_t base; int64_t stride; } backup_t;
 #define BK(bk, t, d) ((bk).p[((t) - (bk).base) + (int64_t)(d) * (bk).stride])
 
+/* w_max N_min of Eq. sab_TA77, or, with duplicity weighting (Sec. 3.2, the alternative of Higginson et al. that
+ * the paper describes), (w_max / D_ij) N_max for inter-species pairs: D_ij is the number of times the particle of
+ * the smaller population in pair k is paired during the interaction. Pair k takes that population's (k mod N_min)-th
+ * particle, which is paired for every k' = k mod N_min in [0, N_max), i.e. D = floor((N_max - 1 - m) / N_min) + 1
+ * with m = k mod N_min. Intra-species pairs keep w_max N_min. */
+static double pair_weight_factor(const orc_params* p, int intra, int64_t na, int64_t nb, int64_t k, double wmax,
+                                 double nmin)
+{
+    if (p->weighting != 1 || intra) return wmax * nmin;
+    int64_t nlo = na < nb ? na : nb, nhi = na < nb ? nb : na;
+    int64_t m = k % nlo;
+    double D = (double)((nhi - 1 - m) / nlo + 1);
+    return wmax / D * (double)nhi;
+}
+
 static void scatter_cell(const state_t* st, int32_t c, const double* q, const double* m, const double* lnL,
                          int32_t sa, int32_t sb, int32_t inter, const orc_params* p, backup_t bk, int* err)
 {
@@ -441,7 +456,7 @@ static void scatter_cell(const state_t* st, int32_t c, const double* q, const do
             double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
             if (u2 == 0.0) continue;
             double umag = sqrt(u2);
-            double s = kappa / (mu * mu) * wmax * nmin / (u2 * umag);
+            double s = kappa / (mu * mu) * pair_weight_factor(p, intra, na, nb, k, wmax, nmin) / (u2 * umag);
             if (fl[k] & PAIR_TRIPLET) s *= 0.5;
             double st_, omc, du[3];
             orc_angle(p->method, s, U1, U4, &st_, &omc);
@@ -454,7 +469,7 @@ static void scatter_cell(const state_t* st, int32_t c, const double* q, const do
             double V[3], gC, pstar[3], pm, vrel;
             rel_cm(p->c, ma, mb, vi, vj, V, &gC, pstar, &pm, &vrel);
             if (!(pm > 0.0)) continue;
-            double s = kappa * wmax * nmin / (pm * pm * vrel);
+            double s = kappa * pair_weight_factor(p, intra, na, nb, k, wmax, nmin) / (pm * pm * vrel);
             if (fl[k] & PAIR_TRIPLET) s *= 0.5;
             double st_, omc, dp[3];
             orc_angle(p->method, s, U1, U4, &st_, &omc);

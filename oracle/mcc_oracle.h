@@ -41,6 +41,7 @@ typedef struct {
     int32_t correct;         /* 0: scatter only, 1: scatter + moment correction */
     uint64_t seed;
     uint64_t step;
+    int32_t weighting;       /* 0: the paper's s (w_max, N_min); 1: duplicity weighting (w_max / D_ij, N_max) */
 } orc_params;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -13,6 +13,7 @@ import pytest
 from scipy import integrate
 
 import oracle as O
+from paper_2407_19151_gb300 import workloads as W
 
 
 def L_ref(A):
@@ -294,3 +295,48 @@ def test_relativistic_scatter_reduces_to_classical():
     np.testing.assert_allclose(dp, mu * du, rtol=1e-9, atol=1e-15)
     assert pstar == pytest.approx(mu * np.linalg.norm(u), rel=1e-10)
     assert vrel == pytest.approx(np.linalg.norm(u), rel=1e-10)
+
+
+def test_duplicity_weighting_pins():
+    """Duplicity weighting (the alternative of Higginson et al. described in Sec. 3.2): s uses (w_max / D_ij) N_max for
+    inter-species pairs, D_ij = how often the smaller population's particle of the pair is paired. One cell with
+    N_a = 3, N_b = 2 and unit weights: pairs 0 and 2 share b's first particle (D = 2), pair 1 has D = 1, so s is the
+    paper's s times 3/4 and 3/2. The scatter with duplicity weighting therefore equals, particle by particle, the
+    paper's scatter with lnL scaled by 3/4 (particles of pairs 0 and 2) and by 3/2 (particles of pair 1)."""
+    rng = np.random.default_rng(8)
+    counts = np.array([[3, 2]])
+    off = np.array([0, 3, 5], dtype=np.int64)
+    v = rng.standard_normal((5, 3))
+    w = np.ones(5)
+    q, m = np.array([-1.0, 1.0]), np.array([1.0, 4.0])
+
+    def run(weighting, lnl):
+        st = O.State(v[:, 0], v[:, 1], v[:, 2], w, off, 1, 2)
+        p = O.Params(method=O.TA77, dt=0.3, seed=21, step=2, correct=False, weighting=weighting)
+        O.step(st, q, m, np.full((2, 2), lnl), p, interactions=[(0, 1)])
+        return st.v()
+
+    pi, pj, fl = O.pairs(off, 1, 2, 0, 1, 0, 21, 2)
+    shared = {int(pi[0]), int(pj[0]), int(pi[2]), int(pj[2])}
+    single = {int(pi[1]), int(pj[1])}
+    assert int(pj[0]) == int(pj[2]) and not (shared & single)
+    h = run(1, 10.0)
+    for idx, scale in ((sorted(shared), 0.75), (sorted(single), 1.5)):
+        ref = run(0, 10.0 * scale)
+        np.testing.assert_allclose(h[idx], ref[idx], rtol=0, atol=1e-12 * np.abs(v).max())
+    # equal to the paper's s when N_min divides N_max in every cell (then D_ij = N_max / N_min for every pair)
+    wl = W.differentiable(n_cells=6, per_species=8)
+    wl.counts[:, 0] = 16
+    wl2 = W.differentiable(n_cells=6, per_species=16)
+    vx = np.concatenate([wl2.vx.reshape(6, 32)[:, :16], wl.vx.reshape(6, 16)[:, 8:]], axis=1).ravel()
+    vy = np.concatenate([wl2.vy.reshape(6, 32)[:, :16], wl.vy.reshape(6, 16)[:, 8:]], axis=1).ravel()
+    vz = np.concatenate([wl2.vz.reshape(6, 32)[:, :16], wl.vz.reshape(6, 16)[:, 8:]], axis=1).ravel()
+    ww = np.concatenate([wl2.w.reshape(6, 32)[:, :16], wl.w.reshape(6, 16)[:, 8:]], axis=1).ravel()
+    off2 = np.zeros(13, dtype=np.int64)
+    off2[1:] = np.cumsum(np.tile([16, 8], 6))
+    out = []
+    for weighting in (0, 1):
+        st = O.State(vx, vy, vz, ww, off2, 6, 2)
+        O.step(st, wl.q, wl.m, wl.lnL, O.Params(method=O.N97, dt=wl.dt * 20, seed=3, weighting=weighting))
+        out.append(st.v())
+    np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-12 * np.abs(out[0]).max())
