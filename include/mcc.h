@@ -87,6 +87,10 @@ typedef struct {
     uint64_t step;
     uint32_t cell_base; /* global id of the first cell (the random counters use global cell ids, so a shard of
                            cells [cell_base, cell_base + n_cells) draws exactly what the unsharded run draws) */
+    int32_t weighting;  /* 0: s with w_max N_min (Eq. sab_TA77); 1: duplicity weighting, the alternative the paper
+                           describes in Sec. 3.2 (Higginson et al.): (w_max / D_ij) N_max for inter-species pairs,
+                           D_ij the number of times the smaller population's particle is paired. mcc_adjoint
+                           requires 0. */
 } mcc_params;
 
 /* Create / destroy a context on `device`. The context owns only a small device buffer (status word, work-queue

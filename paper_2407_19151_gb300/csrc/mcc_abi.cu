@@ -120,6 +120,7 @@ bool valid_params(const mcc_params* p)
     if (!(p->dt > 0) || !(p->dV > 0) || !(p->eps0 > 0) || !(p->fE > 0) || !(p->fE < 1)) return false;
     if (p->relativistic && !(p->c > 0)) return false;
     if (p->max_corr_passes < 0 || p->fail_policy < 0 || p->fail_policy > 2) return false;
+    if (p->weighting != 0 && p->weighting != 1) return false;
     return true;
 }
 
@@ -188,6 +189,7 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
         a.rng.k1 = (uint32_t)(p->seed >> 32);
         a.rng.step = (uint32_t)p->step;
         a.rng.cell_base = p->cell_base;
+        a.weighting = p->weighting;
     }
     a.status = ctx->dbuf;
     a.queue = ctx->dbuf + 1;
@@ -505,7 +507,7 @@ int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
 {
     if (!ctx || !P || !offsets || !sp || !lnL || !valid_params(p) || inter < 0 || inter > 0xFFFFFF || max_cell < 0)
         return MCC_ERR_INVALID_ARG;
-    if (P->prec != MCC_F64 || p->relativistic) return MCC_ERR_INVALID_ARG;
+    if (P->prec != MCC_F64 || p->relativistic || p->weighting != 0) return MCC_ERR_INVALID_ARG;
     const bool fwd = vx_out || vy_out || vz_out, rev = gvx || gvy || gvz;
     if (fwd && !(vx_out && vy_out && vz_out)) return MCC_ERR_INVALID_ARG;
     if (rev && !(gvx && gvy && gvz && gw && glnL)) return MCC_ERR_INVALID_ARG;

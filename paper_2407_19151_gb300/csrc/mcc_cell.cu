@@ -466,9 +466,9 @@ __device__ __forceinline__ void add_weight_sums(Acc<float>& a1, Acc<float>& a2, 
 // through (Theta, phi), boost of the change back to the lab frame. Returns dp = p_i' - p_i.
 template <class V>
 __device__ __forceinline__ void rel_pair_dp_cm(const StepArgs& A, const InterConst& ic, const RelCM<V>& cm, V cc,
-                                               V wmax, int nmin, uint8_t f, V U1, V U2, V U4, V dp[3])
+                                               V wf, uint8_t f, V U1, V U2, V U4, V dp[3])
 {
-    V s = pick<V>(ic.kappa, ic.kappa_f) * wmax * (V)nmin / (cm.pmag * cm.pmag * cm.vrel);
+    V s = pick<V>(ic.kappa, ic.kappa_f) * wf / (cm.pmag * cm.pmag * cm.vrel);
     if (f & kPairTriplet) s *= (V)0.5;
     V st, omc, sp, cp, dx, dy, dz;
     N97Tab<V> tab;
@@ -485,7 +485,7 @@ __device__ __forceinline__ void rel_pair_dp_cm(const StepArgs& A, const InterCon
 
 template <class V>
 __device__ __noinline__ void rel_pair_dp(const StepArgs& A, const InterConst& ic, const V vi[3], const V vj[3],
-                                         V wmax, int nmin, uint8_t f, V U1, V U2, V U4, V dp[3])
+                                         V wf, uint8_t f, V U1, V U2, V U4, V dp[3])
 {
     const V cc = pick<V>(A.c, A.c_f);
     const V ma = pick<V>(A.ma[ic.a], A.ma_f[ic.a]), mb = pick<V>(A.ma[ic.b], A.ma_f[ic.b]);
@@ -494,18 +494,23 @@ __device__ __noinline__ void rel_pair_dp(const StepArgs& A, const InterConst& ic
         dp[0] = dp[1] = dp[2] = (V)0;
         return;
     }
-    rel_pair_dp_cm<V>(A, ic, cm, cc, wmax, nmin, f, U1, U2, U4, dp);
+    rel_pair_dp_cm<V>(A, ic, cm, cc, wf, f, U1, U2, U4, dp);
 }
 
 // One scattering pair (Algorithm 1 pair loop).
 template <class V, bool REL>
 __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t, int c, int64_t cs, uint32_t ictr,
-                                             const InterConst& ic, int p, int i, int j, uint8_t f, int nmin)
+                                             const InterConst& ic, int p, int i, int j, uint8_t f, int nmin,
+                                             int nmax, int pm)
 {
     V vi[3] = {t.v[i], t.v[t.vs + i], t.v[2 * t.vs + i]};
     V vj[3] = {t.v[j], t.v[t.vs + j], t.v[2 * t.vs + j]};
     const V wi = wv(t, i), wj = wv(t, j);
     const V wmax = wi > wj ? wi : wj;
+    // w_max N_min of Eq. sab_TA77, or with duplicity weighting (w_max / D_ij) N_max for an inter-species pair: the
+    // smaller population's particle of pair p (index pm = p mod N_min) is paired D = (N_max - 1 - pm) / N_min + 1 times
+    V wf = wmax * (V)nmin;
+    if (A.weighting == 1 && nmax > 0) wf = wmax / (V)((nmax - 1 - pm) / nmin + 1) * (V)nmax;
     const uint4 r = draw(A.rng, (uint32_t)p, (uint32_t)c, ictr, kTagScat);
     const V U1 = u23<V>(r.x), U2 = u23<V>(r.y), U4 = u23<V>(r.w);
     V dvi[3], dvj[3];
@@ -514,7 +519,7 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
         const V u2 = ux * ux + uy * uy + uz * uz;
         if (u2 == (V)0) return;
         const V um = sqrt(u2);
-        V s = pick<V>(ic.kappa_mu2, ic.kappa_mu2_f) * wmax * (V)nmin / (u2 * um);
+        V s = pick<V>(ic.kappa_mu2, ic.kappa_mu2_f) * wf / (u2 * um);
         if (f & kPairTriplet) s *= (V)0.5;
         V st, omc, sp, cp, dx, dy, dz;
         N97Tab<V> tab;
@@ -537,7 +542,7 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
             // a fast-moving CM frame amplifies float rounding by ~gamma_C^2: this pair's kinematics run in double
             const double vid[3] = {vi[0], vi[1], vi[2]}, vjd[3] = {vj[0], vj[1], vj[2]};
             double dd[3];
-            rel_pair_dp<double>(A, ic, vid, vjd, (double)wmax, nmin, f, u23<double>(r.x), u23<double>(r.y),
+            rel_pair_dp<double>(A, ic, vid, vjd, (double)wf, f, u23<double>(r.x), u23<double>(r.y),
                                 u23<double>(r.w), dd);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -547,7 +552,7 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
         } else {
             if (!(cm.pmag > (V)0)) return;
             V dp[3];
-            rel_pair_dp_cm<V>(A, ic, cm, cc, wmax, nmin, f, U1, U2, U4, dp);
+            rel_pair_dp_cm<V>(A, ic, cm, cc, wf, f, U1, U2, U4, dp);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 dvi[d] = dp[d] / ma;
@@ -850,7 +855,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
                 int i, j;
                 uint8_t f;
                 get(p, p - r0, i, j, f);
-                scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin);
+                scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin, intra ? 0 : npairs, p - r0);
                 p = (p + 1 < lead) ? p + 1 : (p < lead ? lead + (int)threadIdx.x : p + kThreads);
             }
             __syncthreads();

@@ -174,6 +174,9 @@ FUSED_F64 = [
     ("tied_weights", lambda: _tied(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
     ("large_segments", lambda: W.differentiable(n_cells=4, per_species=1500), {}),
     ("weight_ordered", lambda: W.three_species(n_cells=64, mean_count=90, precision="f64").weight_ordered(), {}),
+    ("duplicity_weighting", lambda: W.three_species(n_cells=64, mean_count=90, precision="f64"), {"weighting": 1}),
+    ("duplicity_ta77", lambda: W.equilibration(n_cells=48, mean_count=40, precision="f64", method=W.TA77),
+     {"weighting": 1, "dt_scale": 5}),
     ("ordered_key_ties", lambda: _key_ties(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
 ]
 
