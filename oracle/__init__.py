@@ -46,6 +46,7 @@ class _Params(C.Structure):
         ("dt", C.c_double), ("dV", C.c_double), ("eps0", C.c_double), ("c", C.c_double), ("fE", C.c_double),
         ("sort_by_weight", C.c_int32), ("max_corr_passes", C.c_int32), ("fail_policy", C.c_int32),
         ("correct", C.c_int32), ("seed", C.c_uint64), ("step", C.c_uint64), ("weighting", C.c_int32),
+        ("pairing", C.c_int32),
     ]
 
 
@@ -66,12 +67,14 @@ class Params:
     seed: int = 0
     step: int = 0
     weighting: int = 0   # 0: the paper's s; 1: duplicity weighting (w_max / D_ij, N_max) for inter-species pairs
+    pairing: int = 0     # 0: order-N pairs (Eq. sab_TA77); 1: all N x N pairs (Eq. sab_weighted)
 
     def _c(self) -> _Params:
         return _Params(int(self.method), int(bool(self.relativistic)), float(self.dt), float(self.dV),
                        float(self.eps0), float(self.c), float(self.fE), int(bool(self.sort_by_weight)),
                        int(self.max_corr_passes), int(self.fail_policy), int(bool(self.correct)),
-                       int(self.seed) & (2**64 - 1), int(self.step) & (2**64 - 1), int(self.weighting))
+                       int(self.seed) & (2**64 - 1), int(self.step) & (2**64 - 1), int(self.weighting),
+                       int(self.pairing))
 
 
 _lib = None
@@ -87,6 +90,8 @@ def lib():
             "orc_philox4x32_10": (None, [u32, u32, u32]),
             "orc_bin": (C.c_int, [i32, i32, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
             "orc_set_threads": (None, [C.c_int32]),
+            "orc_nxn_slot": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int64, i64, i64]),
+            "orc_nxn_slots": (C.c_int64, [C.c_int64, C.c_int64, C.c_int32, i64]),
             "orc_bin_weighted": (C.c_int, [i32, i32, d, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
             "orc_permutation": (C.c_int, [C.c_int64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                           i32]),
@@ -129,6 +134,19 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
+    return out
+
+
+def nxn_schedule(na: int, nb: int, intra: bool):
+    """The order N x N schedule of one cell: list of (slot, round, local a, local b) before the permutations."""
+    per = np.zeros(1, dtype=np.int64)
+    n = lib().orc_nxn_slots(na, nb, int(intra), _p(per, C.c_int64))
+    out = []
+    a = np.zeros(1, dtype=np.int64)
+    b = np.zeros(1, dtype=np.int64)
+    for k in range(n):
+        if lib().orc_nxn_slot(na, nb, int(intra), k, _p(a, C.c_int64), _p(b, C.c_int64)):
+            out.append((k, k // int(per[0]), int(a[0]), int(b[0])))
     return out
 
 

@@ -145,6 +145,42 @@ int orc_permutation(int64_t n, uint64_t seed, uint64_t step, uint32_t cell, uint
  * ---------------------------------------------------------------------------------------------------------- */
 #define PAIR_TRIPLET 1u
 
+/* Order N x N schedule (Sec. 3.1: every particle of alpha meets every particle of beta once per step). */
+int64_t orc_nxn_slots(int64_t na, int64_t nb, int32_t intra, int64_t* per_round)
+{
+    if (intra) {
+        if (na < 2) { *per_round = 0; return 0; }
+        int64_t M = na + (na & 1);
+        *per_round = M / 2;
+        return (M - 1) * (M / 2);
+    }
+    if (na == 0 || nb == 0) { *per_round = 0; return 0; }
+    int64_t lo = na < nb ? na : nb, hi = na < nb ? nb : na;
+    *per_round = lo;
+    return lo * hi;
+}
+
+int orc_nxn_slot(int64_t na, int64_t nb, int32_t intra, int64_t k, int64_t* ia, int64_t* jb)
+{
+    if (intra) {
+        int64_t M = na + (na & 1), half = M / 2;
+        int64_t r = k / half, t = k % half;
+        int64_t a, b;
+        if (t == 0) { a = r; b = M - 1; }
+        else { a = (r + t) % (M - 1); b = (r - t + (M - 1)) % (M - 1); }
+        if (a >= na || b >= na) return 0; /* the idle player of an odd count */
+        *ia = a;
+        *jb = b;
+        return 1;
+    }
+    int64_t lo = na < nb ? na : nb, hi = na < nb ? nb : na;
+    int64_t r = k / lo, m = k % lo;
+    int64_t big = (m + r) % hi;
+    if (na >= nb) { *ia = big; *jb = m; }
+    else { *ia = m; *jb = big; }
+    return 1;
+}
+
 static int64_t cell_pair_list(int64_t na, int64_t nb, int intra, uint64_t seed, uint64_t step, uint32_t cell,
                               uint32_t inter, int32_t* li, int32_t* lj, uint8_t* fl, int* err)
 {
@@ -410,7 +446,7 @@ typedef struct { double* p; int64_t base; int64_t stride; } backup_t;
 static double pair_weight_factor(const orc_params* p, int intra, int64_t na, int64_t nb, int64_t k, double wmax,
                                  double nmin)
 {
-    if (p->weighting != 1 || intra) return wmax * nmin;
+    if (p->weighting != 1 || intra || p->pairing == 1) return wmax * nmin;
     int64_t nlo = na < nb ? na : nb, nhi = na < nb ? nb : na;
     int64_t m = k % nlo;
     double D = (double)((nhi - 1 - m) / nlo + 1);
@@ -431,12 +467,37 @@ static void scatter_cell(const state_t* st, int32_t c, const double* q, const do
             BK(bk, t, 0) = st->vx[t]; BK(bk, t, 1) = st->vy[t]; BK(bk, t, 2) = st->vz[t];
         }
     }
-    int64_t cap = na + (intra ? 0 : nb) + 3;
+    int64_t per = 0;
+    int64_t nxn = p->pairing == 1 ? orc_nxn_slots(na, nb, intra, &per) : 0;
+    int64_t cap = (p->pairing == 1 ? nxn : na + (intra ? 0 : nb)) + 3;
     int32_t* li = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
     int32_t* lj = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
     uint8_t* fl = (uint8_t*)malloc((size_t)cap);
-    int64_t np = cell_pair_list(na, nb, intra, p->seed, p->step, (uint32_t)c, (uint32_t)inter, li, lj, fl, err);
-    double nmin = intra ? (double)(na - 1) : (double)(na < nb ? na : nb);
+    int64_t* lk = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t np = 0;
+    if (p->pairing == 1) {
+        /* Eq. sab_weighted: every pair once, slot k of the schedule over the interaction's random permutations,
+         * the draw keyed by the slot */
+        int32_t* pa = (int32_t*)malloc(sizeof(int32_t) * (size_t)(na > 0 ? na : 1));
+        int32_t* pb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+        if (na > 0) orc_permutation(na, p->seed, p->step, (uint32_t)c, (uint32_t)inter, 0, pa);
+        if (!intra && nb > 0) orc_permutation(nb, p->seed, p->step, (uint32_t)c, (uint32_t)inter, 1, pb);
+        for (int64_t k = 0; k < nxn; ++k) {
+            int64_t a, b;
+            if (!orc_nxn_slot(na, nb, intra, k, &a, &b)) continue;
+            li[np] = pa[a];
+            lj[np] = intra ? pa[b] : pb[b];
+            fl[np] = 0;
+            lk[np] = k;
+            ++np;
+        }
+        free(pa);
+        free(pb);
+    } else {
+        np = cell_pair_list(na, nb, intra, p->seed, p->step, (uint32_t)c, (uint32_t)inter, li, lj, fl, err);
+        for (int64_t k = 0; k < np; ++k) lk[k] = k;
+    }
+    double nmin = p->pairing == 1 ? 1.0 : (intra ? (double)(na - 1) : (double)(na < nb ? na : nb));
     double ma = m[sa], mb = m[sb];
     double mu = ma * mb / (ma + mb);
     double kappa = q[sa] * q[sa] * q[sb] * q[sb] * lnL[sa * st->S + sb] * p->dt /
@@ -448,7 +509,7 @@ static void scatter_cell(const state_t* st, int32_t c, const double* q, const do
         double wi = st->w[i], wj = st->w[j];
         double wmax = wi > wj ? wi : wj, wmin = wi > wj ? wj : wi;
         uint32_t r[4];
-        draw(p->seed, (uint32_t)k, (uint32_t)c, p->step, (uint32_t)inter, TAG_SCAT, r);
+        draw(p->seed, (uint32_t)lk[k], (uint32_t)c, p->step, (uint32_t)inter, TAG_SCAT, r);
         double U1 = u23(r[0]), U2 = u23(r[1]), U3 = u23(r[2]), U4 = u23(r[3]);
         double dvi[3], dvj[3];
         if (!p->relativistic) {
@@ -485,7 +546,7 @@ static void scatter_cell(const state_t* st, int32_t c, const double* q, const do
         if (upd_i) { st->vx[i] += dvi[0]; st->vy[i] += dvi[1]; st->vz[i] += dvi[2]; }
         if (upd_j) { st->vx[j] += dvj[0]; st->vy[j] += dvj[1]; st->vz[j] += dvj[2]; }
     }
-    free(li); free(lj); free(fl);
+    free(li); free(lj); free(fl); free(lk);
 }
 
 static int64_t total_n(const int64_t* offsets, int32_t n_cells, int32_t n_species)

@@ -10,6 +10,7 @@
  *   orc_philox4x32_10      pinned: published Philox-4x32-10 known-answer values.
  *   orc_bin                pinned: equals a stable library sort by (cell, species).
  *   orc_bin_weighted       pinned: equals a library lexicographic sort by (cell, species, truncated weight, index).
+ *   orc_nxn_slot           pinned: brute force, every pair of the cell exactly once, rounds disjoint.
  *   orc_pairs              pinned: brute-force structure checks and pairing-uniformity chi-square.
  *   orc_n97_A / angles     pinned: E[cos chi] = exp(-s) by quadrature, asymptotic limits, TA77 variance.
  *   orc_scatter            pinned: expected drag of Eqs. sb_TA_weighted / sa_TA77_weighted, isotropisation and
@@ -42,6 +43,7 @@ typedef struct {
     uint64_t seed;
     uint64_t step;
     int32_t weighting;       /* 0: the paper's s (w_max, N_min); 1: duplicity weighting (w_max / D_ij, N_max) */
+    int32_t pairing;         /* 0: order-N pairs (Eq. sab_TA77); 1: all N x N pairs (Eq. sab_weighted) */
 } orc_params;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -51,6 +53,13 @@ int orc_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_ce
 
 int orc_bin_weighted(const int32_t* cell, const int32_t* species, const double* w, int64_t n, int32_t n_cells,
                      int32_t n_species, int32_t* perm_out, int64_t* offsets_out);
+
+/* k-th pair slot of the order N x N schedule of a cell (local indices before the random permutations are applied):
+ * inter: round r = k / N_min pairs the smaller population's m = k mod N_min with the larger one's (m + r) mod N_max;
+ * intra: a round-robin tournament over N players (plus an idle player when N is odd), N/2 (rounded up) slots a round.
+ * Returns 0 for a slot that pairs a particle with the idle player (no pair). */
+int orc_nxn_slot(int64_t na, int64_t nb, int32_t intra, int64_t k, int64_t* ia, int64_t* jb);
+int64_t orc_nxn_slots(int64_t na, int64_t nb, int32_t intra, int64_t* per_round);
 
 int orc_permutation(int64_t n, uint64_t seed, uint64_t step, uint32_t cell, uint32_t inter, uint32_t side,
                     int32_t* perm_out);

@@ -340,3 +340,79 @@ def test_duplicity_weighting_pins():
         O.step(st, wl.q, wl.m, wl.lnL, O.Params(method=O.N97, dt=wl.dt * 20, seed=3, weighting=weighting))
         out.append(st.v())
     np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-12 * np.abs(out[0]).max())
+
+
+@pytest.mark.parametrize("na,nb,intra", [(2, 0, True), (3, 0, True), (8, 0, True), (9, 0, True), (1, 1, False),
+                                         (3, 5, False), (5, 3, False), (4, 4, False), (7, 2, False)])
+def test_nxn_schedule_covers_every_pair_once(na, nb, intra):
+    """Order N x N pairing (Sec. 3.1): every pair of the cell exactly once per step, the pairs of a round disjoint."""
+    sched = O.nxn_schedule(na, nb, intra)
+    pairs = [(min(a, b), max(a, b)) if intra else (a, b) for _, _, a, b in sched]
+    want = ({(i, j) for i in range(na) for j in range(i + 1, na)} if intra else
+            {(i, j) for i in range(na) for j in range(nb)})
+    assert len(pairs) == len(want) and set(pairs) == want
+    rounds = {}
+    for _, r, a, b in sched:
+        rounds.setdefault(r, []).append((("a", a), ("a" if intra else "b", b)))
+    for r, ps in rounds.items():
+        touched = [x for p in ps for x in p]
+        assert len(touched) == len(set(touched)), r
+
+
+@pytest.mark.parametrize("method", [O.TA77, O.N97])
+def test_nxn_drag_expectation(method):
+    """Mean dv of every particle over many draws in the order N x N mode equals the sum over all partners of the
+    single-pair expectation with s = kappa w_max / (mu^2 u^3) (Eq. sab_weighted) and the rejection of the heavier
+    particle. Species b drifts by 3 so that every pair has s < 1e-2: the order of a particle's pairs within the step
+    is then a second-order effect."""
+    rng = np.random.default_rng(7)
+    n = 4
+    ma, mb, qa, qb = 1.0, 4.0, -1.0, 2.0
+    v = rng.normal(size=(2 * n, 3))
+    v[n:] *= 0.5
+    v[n:, 0] += 3.0
+    w = np.array([1.0, 3.0, 10.0, 0.5, 2.0, 2.0, 7.0, 0.3])
+    M = 30000
+    st = replicate(v, w, [n, n], M)
+    lnL, dt = 10.0, 2e-3
+    p = O.Params(method=method, dt=dt, correct=False, seed=99, pairing=1)
+    O.scatter(st, [qa, qb], [ma, mb], lnL, 0, 1, 0, p)
+    dv = (st.v() - np.tile(v, (M, 1))).reshape(M, 2 * n, 3)
+    mean, se = dv.mean(axis=0), dv.std(axis=0) / math.sqrt(M)
+    mu = ma * mb / (ma + mb)
+    kappa = qa ** 2 * qb ** 2 * lnL * dt / (4 * math.pi)
+    exact = np.zeros((2 * n, 3))
+    for i in range(n):
+        for j in range(n, 2 * n):
+            u = v[i] - v[j]
+            um = np.linalg.norm(u)
+            wmax, wmin = max(w[i], w[j]), min(w[i], w[j])
+            s = kappa / mu ** 2 * wmax / um ** 3
+            Pi = 1.0 if w[i] <= w[j] else wmin / wmax
+            Pj = 1.0 if w[j] <= w[i] else wmin / wmax
+            assert s < 1e-2
+            h = h1_exact(method, s)
+            exact[i] += Pi * (mu / ma) * (-u) * h
+            exact[j] += Pj * (mu / mb) * (u) * h
+    z = (mean - exact) / se
+    assert np.all(np.abs(z) < 5.0), z
+
+
+def test_nxn_equal_weights_conserve_pairwise():
+    """Equal weights: every N x N pair conserves momentum and energy, so the scatter alone conserves them per cell."""
+    wl = W.differentiable(n_cells=4, per_species=10)
+    wl.w[:] = 3.0
+    st = O.State(wl.vx, wl.vy, wl.vz, wl.w, wl.offsets, wl.n_cells, wl.n_species)
+    v0 = st.v().copy()
+    O.step(st, wl.q, wl.m, wl.lnL, O.Params(method=O.N97, dt=wl.dt * 50, seed=4, correct=False, pairing=1))
+    v1 = st.v()
+    sp = wl.species_of_particles()
+    mw = wl.m[sp] * wl.w
+    cells = np.repeat(np.arange(wl.n_cells), np.diff(wl.offsets[::wl.n_species]))
+    for c in range(wl.n_cells):
+        k = cells == c
+        P0, P1 = (mw[k, None] * v0[k]).sum(0), (mw[k, None] * v1[k]).sum(0)
+        E0, E1 = (mw[k] * (v0[k] ** 2).sum(1)).sum(), (mw[k] * (v1[k] ** 2).sum(1)).sum()
+        assert np.abs(P1 - P0).max() < 1e-12 * np.abs(mw[k, None] * v0[k]).sum()
+        assert abs(E1 - E0) < 1e-12 * E0
+    assert np.abs(v1 - v0).max() > 1e-3
