@@ -91,6 +91,11 @@ typedef struct {
                            describes in Sec. 3.2 (Higginson et al.): (w_max / D_ij) N_max for inter-species pairs,
                            D_ij the number of times the smaller population's particle is paired. mcc_adjoint
                            requires 0. */
+    int32_t pairing;    /* 0: order-N pairs (Eq. sab_TA77); 1: order N x N (Sec. 3.1, Eq. sab_weighted): every pair
+                           of the interaction once per step, in rounds of disjoint pairs over the interaction's random
+                           permutations (inter: round r pairs the smaller population's m with the larger one's
+                           (m + r) mod N_max; intra: a round-robin tournament), the draw keyed by the slot, s with
+                           w_max alone. Fused step only: mcc_pair, mcc_scatter and mcc_adjoint require 0. */
 } mcc_params;
 
 /* Create / destroy a context on `device`. The context owns only a small device buffer (status word, work-queue

@@ -40,7 +40,7 @@ class _Params(C.Structure):
                 ("eps0", C.c_double), ("c", C.c_double), ("fE", C.c_double), ("sort_by_weight", C.c_int32),
                 ("max_corr_passes", C.c_int32), ("fail_policy", C.c_int32), ("correct", C.c_int32),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("cell_base", C.c_uint32),
-                ("weighting", C.c_int32)]
+                ("weighting", C.c_int32), ("pairing", C.c_int32)]
 
 
 @dataclass
@@ -61,13 +61,14 @@ class Params:
     step: int = 0
     cell_base: int = 0
     weighting: int = 0   # 0: the paper's s; 1: duplicity weighting (w_max / D_ij, N_max) for inter-species pairs
+    pairing: int = 0     # 0: order-N pairs; 1: all N x N pairs (fused step only)
 
     def _c(self) -> _Params:
         return _Params(int(self.method), int(bool(self.relativistic)), float(self.dt), float(self.dV),
                        float(self.eps0), float(self.c), float(self.fE), int(bool(self.sort_by_weight)),
                        int(self.max_corr_passes), int(self.fail_policy), int(bool(self.correct)),
                        int(self.seed) & (2**64 - 1), int(self.step) & (2**64 - 1), int(self.cell_base),
-                       int(self.weighting))
+                       int(self.weighting), int(self.pairing))
 
 
 _LIB = None

@@ -121,6 +121,7 @@ bool valid_params(const mcc_params* p)
     if (p->relativistic && !(p->c > 0)) return false;
     if (p->max_corr_passes < 0 || p->fail_policy < 0 || p->fail_policy > 2) return false;
     if (p->weighting != 0 && p->weighting != 1) return false;
+    if (p->pairing != 0 && p->pairing != 1) return false;
     return true;
 }
 
@@ -190,6 +191,7 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
         a.rng.step = (uint32_t)p->step;
         a.rng.cell_base = p->cell_base;
         a.weighting = p->weighting;
+        a.pairing = p->pairing;
     }
     a.status = ctx->dbuf;
     a.queue = ctx->dbuf + 1;
@@ -379,7 +381,7 @@ int mcc_scatter(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
                 mcc_stream stream)
 {
     if (!ctx || !P || !offsets || !sp || !lnL || !pair_i || !pair_j || !pair_flags || !backup || !valid_params(p) ||
-        inter < 0 || inter > 0xFFFFFF)
+        inter < 0 || inter > 0xFFFFFF || p->pairing != 0)
         return MCC_ERR_INVALID_ARG;
     if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
@@ -507,7 +509,7 @@ int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
 {
     if (!ctx || !P || !offsets || !sp || !lnL || !valid_params(p) || inter < 0 || inter > 0xFFFFFF || max_cell < 0)
         return MCC_ERR_INVALID_ARG;
-    if (P->prec != MCC_F64 || p->relativistic || p->weighting != 0) return MCC_ERR_INVALID_ARG;
+    if (P->prec != MCC_F64 || p->relativistic || p->weighting != 0 || p->pairing != 0) return MCC_ERR_INVALID_ARG;
     const bool fwd = vx_out || vy_out || vz_out, rev = gvx || gvy || gvz;
     if (fwd && !(vx_out && vy_out && vz_out)) return MCC_ERR_INVALID_ARG;
     if (rev && !(gvx && gvy && gvz && gw && glnL)) return MCC_ERR_INVALID_ARG;

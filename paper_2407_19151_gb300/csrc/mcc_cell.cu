@@ -411,6 +411,36 @@ __device__ __forceinline__ void pair_at(const Tile<V>& t, bool intra, int na, in
     }
 }
 
+// Slot k of the order N x N schedule (local indices into the interaction's permutations). Inter: round k / N_min
+// pairs the smaller population's m = k mod N_min with the larger one's (m + round) mod N_max. Intra: round-robin
+// tournament (circle method) over N players plus an idle one when N is odd; false for a slot with the idle player.
+__device__ __forceinline__ bool nxn_slot(int na, int nb, bool intra, int k, int& a, int& b)
+{
+    if (intra) {
+        const int M = na + (na & 1), half = M / 2;
+        const int r = k / half, q = k - r * half;
+        if (q == 0) {
+            a = r;
+            b = M - 1;
+        } else {
+            a = (r + q) % (M - 1);
+            b = (r - q + (M - 1)) % (M - 1);
+        }
+        return a < na && b < na;
+    }
+    const int lo = na < nb ? na : nb, hi = na < nb ? nb : na;
+    const int r = k / lo, m = k - r * lo;
+    const int big = (m + r) % hi;
+    if (na >= nb) {
+        a = big;
+        b = m;
+    } else {
+        a = m;
+        b = big;
+    }
+    return true;
+}
+
 // Heavier particle of an unequal-weight pair moves iff U3 w_max < w_min, decided in FP64 exactly as the
 // definition states. The mixed path first decides in float with a bound on the float error and falls back to the
 // FP64 test only within that bound of the boundary.
@@ -843,6 +873,20 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
                 pair_at(t, intra, na, nb, a0, b0, p, pm, i, j, f);
             }
         };
+        if (MODE == kFused && A.pairing == 1) {
+            // order N x N (Eq. sab_weighted): every pair once, in rounds of disjoint pairs, s with w_max alone
+            const int per = intra ? (na + (na & 1)) / 2 : (na < nb ? na : nb);
+            const int nslots = intra ? (2 * per - 1) * per : na * nb;
+            for (int r0 = 0; r0 < nslots; r0 += per) {
+                for (int q = threadIdx.x; q < per; q += kThreads) {
+                    int a, b;
+                    if (!nxn_slot(na, nb, intra, r0 + q, a, b)) continue;
+                    const int i = t.perm[a0 + a], j = intra ? t.perm[a0 + b] : t.perm[b0 + b];
+                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, r0 + q, i, j, 0, 1, 0, 0);
+                }
+                __syncthreads();
+            }
+        } else {
         // Intra: one round; an odd count starts with the triplet (pairs 0..2 share particles), run in order by thread
         // 0 while the other threads start on pair 3. Inter: rounds of N_min disjoint pairs, in order. One call site
         // keeps a single inlined copy of the pair code.
@@ -859,6 +903,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
                 p = (p + 1 < lead) ? p + 1 : (p < lead ? lead + (int)threadIdx.x : p + kThreads);
             }
             __syncthreads();
+        }
         }
     }
     if (MODE == kCorrect || (MODE == kFused && A.correct))

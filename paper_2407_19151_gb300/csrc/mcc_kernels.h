@@ -38,6 +38,7 @@ struct StepArgs {
     int32_t inter_base;  // counter index of ic[0] (unfused calls: the interaction's index in the step)
     int32_t method, fail_policy, sort_by_weight, max_corr_passes, correct;
     int32_t weighting;  // 0: w_max N_min in s; 1: duplicity weighting (w_max / D_ij) N_max for inter-species pairs
+    int32_t pairing;    // 0: order-N pairs; 1: all N x N pairs (fused step only)
     double c, fE;
     float c_f, fE_f;
     RngKey rng;

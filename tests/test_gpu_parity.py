@@ -175,6 +175,9 @@ FUSED_F64 = [
     ("large_segments", lambda: W.differentiable(n_cells=4, per_species=1500), {}),
     ("weight_ordered", lambda: W.three_species(n_cells=64, mean_count=90, precision="f64").weight_ordered(), {}),
     ("duplicity_weighting", lambda: W.three_species(n_cells=64, mean_count=90, precision="f64"), {"weighting": 1}),
+    ("nxn_single_species", lambda: W.isotropisation(n_cells=16, per_cell=33), {"pairing": 1}),
+    ("nxn_two_species", lambda: W.equilibration(n_cells=64, mean_count=16, precision="f64"), {"pairing": 1}),
+    ("nxn_three_species", lambda: W.three_species(n_cells=24, mean_count=90, precision="f64"), {"pairing": 1}),
     ("duplicity_ta77", lambda: W.equilibration(n_cells=48, mean_count=40, precision="f64", method=W.TA77),
      {"weighting": 1, "dt_scale": 5}),
     ("ordered_key_ties", lambda: _key_ties(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
