@@ -133,6 +133,7 @@ struct Shared {
                              // (sorted per interaction), 3 stored in strictly descending order (rho = identity)
     int cell;
     int fail;
+    int fast;  // energy pairs of a side finished by the first warp
     alignas(16) unsigned char red_raw[8 * kThreads * 8];  // block_sum partials (8 quantities x 8 bytes)
     alignas(8) unsigned char red[8 * 8];                  // block_sum results (Acc<V>, 8 bytes each)
     double scan_d[kWarps + 1];
@@ -721,7 +722,76 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
         V Dabs = D < (V)0 ? -D : D;
         const V sgn = D > (V)0 ? (V)1 : (V)-1;
         const V fE = pick<V>(A.fE, A.fE_f);
-        bool done = false;
+        // pair m of a pass starting at offset o: its particles, velocities, weighted masses and CM energy K
+        auto load_pair = [&](int o, int m, int& i, int& j, V v1[3], V v2[3], V& m1, V& m2) -> V {
+            i = rho(o + 2 * m);
+            j = rho(o + 2 * m + 1);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                v1[d] = t.v[d * t.vs + i];
+                v2[d] = t.v[d * t.vs + j];
+            }
+            m1 = ms * wv(t, i);
+            m2 = ms * wv(t, j);
+            if (REL && sizeof(V) == 4 && fast_pair(cc, v1, v2)) {
+                const double d1[3] = {v1[0], v1[1], v1[2]}, d2[3] = {v2[0], v2[1], v2[2]};
+                return (V)pair_kecm<double, true>(A.c, A.m[side ? ic.b : ic.a] * w_exact(t, A, cs, i),
+                                                  A.m[side ? ic.b : ic.a] * w_exact(t, A, cs, j), d1, d2);
+            }
+            return pair_kecm<V, REL>(cc, m1, m2, v1, v2);
+        };
+        // the pair takes its cap, or the remainder if it is the crossing pair (excl = caps of the pairs before it)
+        auto apply_pair = [&](int i, int j, V v1[3], V v2[3], V m1, V m2, V K, V capv, V excl) {
+            const V rem = Dabs - excl;
+            const V U = sgn * (rem < capv ? rem : capv);
+            if (REL && sizeof(V) == 4 && fast_pair(cc, v1, v2)) {
+                double d1[3] = {v1[0], v1[1], v1[2]}, d2[3] = {v2[0], v2[1], v2[2]};
+                const double ms_d = A.m[side ? ic.b : ic.a];
+                energy_pair<double, true>(A.c, ms_d * w_exact(t, A, cs, i), ms_d * w_exact(t, A, cs, j), (double)K,
+                                          d1, d2, (double)U);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    v1[d] = (V)d1[d];
+                    v2[d] = (V)d2[d];
+                }
+            } else {
+                energy_pair<V, REL>(cc, m1, m2, K, v1, v2, U);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                t.v[d * t.vs + i] = v1[d];
+                t.v[d * t.vs + j] = v2[d];
+            }
+            ++used;
+        };
+        // The crossing pair is nearly always among the first 32 pairs of the first pass: one warp computes their caps
+        // and their prefix sum (the same sums, in the same order, as the block scan below) and finishes the side if
+        // they absorb |Delta E_s|; otherwise nothing was applied and the block loop runs from the start.
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const int np0 = ns / 2;
+            const bool valid = lane < np0;
+            int i = 0, j = 0;
+            V v1[3] = {0, 0, 0}, v2[3] = {0, 0, 0}, K = 0, capv = 0, m1 = 1, m2 = 1;
+            if (valid) {
+                K = load_pair(0, lane, i, j, v1, v2, m1, m2);
+                capv = K > (V)0 ? fE * K : (V)0;
+            }
+            V inc = capv;
+#pragma unroll
+            for (int s1 = 1; s1 < 32; s1 <<= 1) {
+                const V y = __shfl_up_sync(0xffffffffu, inc, s1);
+                if (lane >= s1) inc += y;
+            }
+            V excl = __shfl_up_sync(0xffffffffu, inc, 1);
+            if (lane == 0) excl = (V)0;
+            const V tot = __shfl_sync(0xffffffffu, inc, 31);
+            const bool fast = tot >= Dabs;
+            if (fast && valid && K > (V)0 && excl < Dabs) apply_pair(i, j, v1, v2, m1, m2, K, capv, excl);
+            if (lane == 0) sh.fast = fast;
+        }
+        __syncthreads();
+        bool done = sh.fast;
         for (int pass = 0; pass < A.max_corr_passes && !done; ++pass) {
             const int o = pass & 1;
             const int np = (ns - o) / 2;
@@ -732,49 +802,12 @@ __device__ void correct_interaction(const StepArgs& A, const Tile<V>& t, Shared&
                 int i = 0, j = 0;
                 V v1[3] = {0, 0, 0}, v2[3] = {0, 0, 0}, K = 0, capv = 0, m1 = 1, m2 = 1;
                 if (valid) {
-                    i = rho(o + 2 * m);
-                    j = rho(o + 2 * m + 1);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        v1[d] = t.v[d * t.vs + i];
-                        v2[d] = t.v[d * t.vs + j];
-                    }
-                    m1 = ms * wv(t, i);
-                    m2 = ms * wv(t, j);
-                    if (REL && sizeof(V) == 4 && fast_pair(cc, v1, v2)) {
-                        const double d1[3] = {v1[0], v1[1], v1[2]}, d2[3] = {v2[0], v2[1], v2[2]};
-                        K = (V)pair_kecm<double, true>(A.c, A.m[side ? ic.b : ic.a] * w_exact(t, A, cs, i),
-                                                       A.m[side ? ic.b : ic.a] * w_exact(t, A, cs, j), d1, d2);
-                    } else {
-                        K = pair_kecm<V, REL>(cc, m1, m2, v1, v2);
-                    }
+                    K = load_pair(o, m, i, j, v1, v2, m1, m2);
                     capv = K > (V)0 ? fE * K : (V)0;
                 }
                 V total;
                 const V excl = block_exclusive_scan<V>(capv, scan_scratch<V>(sh), total) + carry;
-                if (valid && K > (V)0 && excl < Dabs) {
-                    const V rem = Dabs - excl;
-                    const V U = sgn * (rem < capv ? rem : capv);
-                    if (REL && sizeof(V) == 4 && fast_pair(cc, v1, v2)) {
-                        double d1[3] = {v1[0], v1[1], v1[2]}, d2[3] = {v2[0], v2[1], v2[2]};
-                        const double ms_d = A.m[side ? ic.b : ic.a];
-                        energy_pair<double, true>(A.c, ms_d * w_exact(t, A, cs, i), ms_d * w_exact(t, A, cs, j),
-                                                  (double)K, d1, d2, (double)U);
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            v1[d] = (V)d1[d];
-                            v2[d] = (V)d2[d];
-                        }
-                    } else {
-                        energy_pair<V, REL>(cc, m1, m2, K, v1, v2, U);
-                    }
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        t.v[d * t.vs + i] = v1[d];
-                        t.v[d * t.vs + j] = v2[d];
-                    }
-                    ++used;
-                }
+                if (valid && K > (V)0 && excl < Dabs) apply_pair(i, j, v1, v2, m1, m2, K, capv, excl);
                 carry += total;
                 if (carry >= Dabs) done = true;
             }
