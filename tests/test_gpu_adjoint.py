@@ -172,3 +172,22 @@ def test_adjoint_fp32_variant(mcc):
     g64, g32 = res[torch.float64], res[torch.float32]
     for a, b in zip(g32, g64):
         assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max()
+
+
+def test_adjoint_rejects_unsupported_steps(mcc):
+    """The adjoint covers the FP64, non-relativistic step with the paper's s and order-N pairs; anything else is an
+    argument error before any launch."""
+    import torch
+    wl, kw = _case(W.N97)
+    v, w, off, _ = _tensors(wl)
+    sp = list(zip(wl.q.tolist(), wl.m.tolist()))
+    mc = int(wl.counts.sum(1).max())
+    out = [torch.empty_like(x) for x in v]
+    for bad in ({"relativistic": True}, {"weighting": 1}, {"pairing": 1}):
+        with pytest.raises(mcc.MccError) as e:
+            mcc.mcc_adjoint(*v, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, 0, 1, 1, mcc.Params(**kw, **bad), mc,
+                            out=out)
+        assert e.value.code == -1
+    vf = [x.float() for x in v]
+    with pytest.raises(mcc.MccError):
+        mcc.mcc_adjoint(*vf, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, 0, 1, 1, mcc.Params(**kw), mc, out=out)
