@@ -78,19 +78,24 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken on this kernel
-    source; otherwise None."""
+def ncu_entry(workload: str):
+    """The committed ncu summary of the step kernel (DRAM bytes per launch, issue-slot use), if it was taken on this
+    kernel source; otherwise None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(workload)
         if e and e.get("kernel_source") == kernel_source_hash():
-            return float(e["dram_bytes_per_launch"])
+            return e
     except Exception:
         pass
     return None
+
+
+def ncu_traffic(workload: str):
+    e = ncu_entry(workload)
+    return float(e["dram_bytes_per_launch"]) if e else None
 
 
 class ClockSampler:
@@ -431,7 +436,9 @@ def run_ours(args):
                    "parallelism": f"cells, {world} independent shard(s)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes": f"{BYTES_PER_PARTICLE['f32']} B/particle x {N} particles per launch"},
+                     "algorithmic_bytes": f"{BYTES_PER_PARTICLE['f32']} B/particle x {N} particles per launch",
+                     "issue_slots_busy": (ncu_entry("three_species") or {}).get("issue_slots_busy"),
+                     "note": "latency- and issue-bound (block barriers per interaction), not HBM-bound"},
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": args.steps + 1,  # one persistent step kernel per captured step + the cell-order kernel
