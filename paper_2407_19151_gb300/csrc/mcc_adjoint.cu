@@ -13,6 +13,8 @@
 //            U = D - (sum of the earlier pairs' U); v1' = v1 + m2/M (g - 1) v_R, v2' = v2 - m1/M (g - 1) v_R,
 //            g = sqrt(1 - U/K);
 //   rollback (Sec. 5.2) when the correction fails: v_after = v_before.
+// A Delta E_s that vanishes (equal weights, or below the rounding-noise threshold) is differentiated as its limit:
+// the first pair of the order as the crossing pair with U = Delta E_s = 0.
 // The kernel recomputes the interaction from the stored pre-interaction state, keeping a tape of every pair's inputs,
 // then runs the chain rule backwards through the tape (one CTA per cell, the cell's working arrays in a per-CTA slab
 // of the workspace).
@@ -499,9 +501,38 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ Ad
                     for (int side = 0; side < nside; ++side) {
                         sh.e0[side] = e;
                         sh.ne[side] = 0;
-                        if (sh.fail || sh.D[side] == 0.0) continue;
+                        if (sh.fail) continue;
                         const int s0 = side ? b0 : a0, ns = side ? nb : na;
                         const double msd = ms[side];
+                        if (sh.D[side] == 0.0) {
+                            // Delta E_s vanishes here (exactly, or as rounding noise), so the step applies no energy
+                            // pair; but it moves at first order with v and w, and then the first pair of the order
+                            // absorbs it as the crossing pair. Tape that pair with U = 0 (no change in the forward).
+                            for (int t = 0; t + 1 < ns; t += 2) {
+                                const int i = sl.rho[s0 + t], j = sl.rho[s0 + t + 1];
+                                double v1[3], v2[3];
+                                ld3(sl.v, N, i, v1);
+                                ld3(sl.v, N, j, v2);
+                                const double K =
+                                    pair_kecm<double, false>(A.c, msd * wg[cs + i], msd * wg[cs + j], v1, v2);
+                                if (!(K > 0.0)) continue;
+                                if (e < sl.E) {
+                                    for (int k = 0; k < 3; ++k) {
+                                        sl.ev[k * sl.E + e] = v1[k];
+                                        sl.ev[(3 + k) * sl.E + e] = v2[k];
+                                    }
+                                    sl.ei[e] = i;
+                                    sl.ej[e] = j;
+                                    sl.eU[e] = 0.0;
+                                    sl.eK[e] = K;
+                                    sl.ecap[e] = 0;
+                                    ++e;
+                                    ++sh.ne[side];
+                                }
+                                break;
+                            }
+                            continue;
+                        }
                         double D = sh.D[side];
                         for (int pass = 0; pass < A.max_corr_passes && D != 0.0; ++pass) {
                             for (int t = pass & 1; t + 1 < ns && D != 0.0; t += 2) {
@@ -633,8 +664,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ Ad
                     }
                     // Delta E split backwards
                     double gdE = 0.0, gE0 = 0.0, gE1 = 0.0, gW0 = 0.0, gW1 = 0.0;
-                    const double g0 = sh.zeroed[0] ? 0.0 : sh.gD[0];
-                    const double g1 = (intra || sh.zeroed[1]) ? 0.0 : sh.gD[1];
+                    const double g0 = sh.gD[0];
+                    const double g1 = intra ? 0.0 : sh.gD[1];
                     if (intra) {
                         gdE = g0;
                     } else {
