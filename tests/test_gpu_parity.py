@@ -259,6 +259,28 @@ def test_fused_mixed_precision(mcc, name, make, p99, bound):
     assert err[ok].max() < bound, err[ok].max()
 
 
+@pytest.mark.parametrize("name,make,kw,scatter_max", [
+    ("duplicity_weighting", lambda: W.three_species(n_cells=200, mean_count=120), {"weighting": 1}, F32_TOL),
+    ("nxn_two_species", lambda: W.equilibration(n_cells=100, mean_count=12, precision="f32"), {"pairing": 1}, 1e-5),
+], ids=["duplicity_weighting", "nxn_two_species"])
+def test_fused_mixed_precision_options(mcc, name, make, kw, scatter_max):
+    """Mixed path with the step's options: the scatter within 2e-6 of the FP64 oracle for 99% of particles and for
+    every particle of the order-N pairing (in the N x N pairing each particle is scattered by every partner in turn, so
+    float rounding accumulates over ~N partners: every particle within 1e-5), and the whole step within 2e-6 for 99%
+    of particles (the bound of the non-relativistic whole-step test)."""
+    wl = make()
+    got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f32", n_steps=1, correct=False, **dict(kw))
+    err = velocity_error(got, ref, wl.offsets)
+    assert np.quantile(err, 0.99) < F32_TOL
+    assert err.max() < scatter_max, err.max()
+    got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f32", n_steps=1, **dict(kw))
+    err = velocity_error(got, ref, wl.offsets)
+    ok = np.repeat(fail == rf, np.diff(wl.offsets[::wl.n_species]))
+    assert ok.mean() >= 0.98
+    assert np.quantile(err[ok], 0.99) < F32_TOL
+    assert err[ok].max() < 2e-4
+
+
 def test_fused_slab_path_matches_tile(mcc):
     """Cells larger than the on-chip tile run from the workspace slabs and give the same result."""
     wl = W.three_species(n_cells=40, mean_count=300, precision="f64")
