@@ -96,6 +96,9 @@ typedef struct {
                            permutations (inter: round r pairs the smaller population's m with the larger one's
                            (m + r) mod N_max; intra: a round-robin tournament), the draw keyed by the slot, s with
                            w_max alone. Fused step only: mcc_pair, mcc_scatter and mcc_adjoint require 0. */
+    uint64_t* step_device; /* mcc_step_fused only (null: use step): the step index lives in device memory; step t of
+                              a call draws with *step_device + t, and the call adds n_steps to it on its stream after
+                              the last step, so that a CUDA graph captured from one call serves every later step */
 } mcc_params;
 
 /* Create / destroy a context on `device`. The context owns only a small device buffer (status word, work-queue

@@ -40,7 +40,7 @@ class _Params(C.Structure):
                 ("eps0", C.c_double), ("c", C.c_double), ("fE", C.c_double), ("sort_by_weight", C.c_int32),
                 ("max_corr_passes", C.c_int32), ("fail_policy", C.c_int32), ("correct", C.c_int32),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("cell_base", C.c_uint32),
-                ("weighting", C.c_int32), ("pairing", C.c_int32)]
+                ("weighting", C.c_int32), ("pairing", C.c_int32), ("step_device", C.c_void_p)]
 
 
 @dataclass
@@ -62,13 +62,15 @@ class Params:
     cell_base: int = 0
     weighting: int = 0   # 0: the paper's s; 1: duplicity weighting (w_max / D_ij, N_max) for inter-species pairs
     pairing: int = 0     # 0: order-N pairs; 1: all N x N pairs (fused step only)
+    step_device: object = None  # optional int64/uint64 device tensor of one element holding the step (fused step)
 
     def _c(self) -> _Params:
         return _Params(int(self.method), int(bool(self.relativistic)), float(self.dt), float(self.dV),
                        float(self.eps0), float(self.c), float(self.fE), int(bool(self.sort_by_weight)),
                        int(self.max_corr_passes), int(self.fail_policy), int(bool(self.correct)),
                        int(self.seed) & (2**64 - 1), int(self.step) & (2**64 - 1), int(self.cell_base),
-                       int(self.weighting), int(self.pairing))
+                       int(self.weighting), int(self.pairing),
+                       C.c_void_p(self.step_device.data_ptr()) if self.step_device is not None else C.c_void_p(0))
 
 
 _LIB = None

@@ -483,10 +483,16 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
     if (mcc::launch_cell_order(offsets, n_cells, n_species, order, S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
     ctx->launches += 1;
     a.order = order;
+    a.step_dev = p->step_device;
     for (int32_t t = 0; t < n_steps; ++t) {
         a.rng.step = (uint32_t)(p->step + (uint64_t)t);
+        a.step_add = (uint32_t)t;
         rc = run_cells(ctx, a, f32, rel, mcc::kFused, cap, S(stream), max_grid);
         if (rc != MCC_OK) return rc;
+    }
+    if (p->step_device) {
+        if (mcc::launch_step_advance(p->step_device, (uint64_t)n_steps, S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
+        ctx->launches += 1;
     }
     return MCC_OK;
 }

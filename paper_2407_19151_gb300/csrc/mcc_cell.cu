@@ -132,6 +132,7 @@ struct Shared {
     int wmode[kMaxSpecies];  // weight order: 0 distinct (rho fixed for the visit), 1 all equal (rho = perm), 2 ties
                              // (sorted per interaction), 3 stored in strictly descending order (rho = identity)
     int cell;
+    uint32_t step;  // the step index of the random counters (from device memory when the caller keeps it there)
     int fail;
     int fast;  // energy pairs of a side finished by the first warp
     alignas(16) unsigned char red_raw[8 * kThreads * 8];  // block_sum partials (8 quantities x 8 bytes)
@@ -311,7 +312,7 @@ __device__ void permutations(const StepArgs& A, const Tile<V>& t, Shared& sh, in
         const int s0 = s0v[side], n = nv[side];
         const uint32_t tag = side ? kTagPermB : kTagPermA;
         for (int h = threadIdx.x; 2 * h < n; h += kThreads) {
-            const uint4 r = draw(A.rng, (uint32_t)h, (uint32_t)c, ictr, tag);
+            const uint4 r = draw_at(A.rng, sh.step, (uint32_t)h, (uint32_t)c, ictr, tag);
             t.keys[s0 + 2 * h] = ((((uint64_t)r.x << 32) | r.y) & ~kPermMask) | (uint64_t)(2 * h);
             if (2 * h + 1 < n) t.keys[s0 + 2 * h + 1] = ((((uint64_t)r.z << 32) | r.w) & ~kPermMask) | (uint64_t)(2 * h + 1);
         }
@@ -532,7 +533,7 @@ __device__ __noinline__ void rel_pair_dp(const StepArgs& A, const InterConst& ic
 template <class V, bool REL>
 __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t, int c, int64_t cs, uint32_t ictr,
                                              const InterConst& ic, int p, int i, int j, uint8_t f, int nmin,
-                                             int nmax, int pm)
+                                             int nmax, int pm, uint32_t step)
 {
     V vi[3] = {t.v[i], t.v[t.vs + i], t.v[2 * t.vs + i]};
     V vj[3] = {t.v[j], t.v[t.vs + j], t.v[2 * t.vs + j]};
@@ -542,7 +543,7 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
     // smaller population's particle of pair p (index pm = p mod N_min) is paired D = (N_max - 1 - pm) / N_min + 1 times
     V wf = wmax * (V)nmin;
     if (A.weighting == 1 && nmax > 0) wf = wmax / (V)((nmax - 1 - pm) / nmin + 1) * (V)nmax;
-    const uint4 r = draw(A.rng, (uint32_t)p, (uint32_t)c, ictr, kTagScat);
+    const uint4 r = draw_at(A.rng, step, (uint32_t)p, (uint32_t)c, ictr, kTagScat);
     const V U1 = u23<V>(r.x), U2 = u23<V>(r.y), U4 = u23<V>(r.w);
     V dvi[3], dvj[3];
     if (!REL) {
@@ -915,7 +916,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
                     int a, b;
                     if (!nxn_slot(na, nb, intra, r0 + q, a, b)) continue;
                     const int i = t.perm[a0 + a], j = intra ? t.perm[a0 + b] : t.perm[b0 + b];
-                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, r0 + q, i, j, 0, 1, 0, 0);
+                    scatter_pair<V, REL>(A, t, c, cs, ictr, ic, r0 + q, i, j, 0, 1, 0, 0, sh.step);
                 }
                 __syncthreads();
             }
@@ -932,7 +933,7 @@ __device__ void interaction(const StepArgs& A, const Tile<V>& t, Shared& sh, int
                 int i, j;
                 uint8_t f;
                 get(p, p - r0, i, j, f);
-                scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin, intra ? 0 : npairs, p - r0);
+                scatter_pair<V, REL>(A, t, c, cs, ictr, ic, p, i, j, f, nmin, intra ? 0 : npairs, p - r0, sh.step);
                 p = (p + 1 < lead) ? p + 1 : (p < lead ? lead + (int)threadIdx.x : p + kThreads);
             }
             __syncthreads();
@@ -1053,6 +1054,7 @@ __global__ void __launch_bounds__(kThreads, MCC_MIN_BLOCKS) cell_kernel(const __
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ Shared sh;
+    if (threadIdx.x == 0) sh.step = A.step_dev ? (uint32_t)(*A.step_dev + A.step_add) : A.rng.step;
     for (;;) {
         if (threadIdx.x == 0) {
             const int q = atomicAdd(A.queue, 1);
@@ -1064,6 +1066,13 @@ __global__ void __launch_bounds__(kThreads, MCC_MIN_BLOCKS) cell_kernel(const __
         process_cell<V, REL, MODE>(A, c, dyn, sh);
         __syncthreads();
     }
+}
+
+// Advance a step counter kept in device memory (after the steps of one call, so that a captured graph of the call
+// serves every later step).
+__global__ void k_step_advance(uint64_t* step, uint64_t by)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step += by;
 }
 
 // Cells ordered by descending size class (floor(log2 n)), so the persistent CTAs take the largest cells first and
@@ -1145,6 +1154,12 @@ int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem)
         cudaSuccess)
         return 0;
     return blocks;
+}
+
+cudaError_t launch_step_advance(uint64_t* step, uint64_t by, cudaStream_t st)
+{
+    k_step_advance<<<1, 32, 0, st>>>(step, by);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cell_order(const int64_t* offsets, int32_t n_cells, int32_t S, int32_t* order, cudaStream_t st)

@@ -68,6 +68,13 @@ __device__ __forceinline__ uint4 draw(const RngKey& k, uint32_t index, uint32_t 
     return philox4x32_10(index, cell + k.cell_base, k.step, (inter << 8) | purpose, k.k0, k.k1);
 }
 
+// The same block with the step index given apart (read from device memory by the caller when it keeps it there).
+__device__ __forceinline__ uint4 draw_at(const RngKey& k, uint32_t step, uint32_t index, uint32_t cell, uint32_t inter,
+                                         uint32_t purpose)
+{
+    return philox4x32_10(index, cell + k.cell_base, step, (inter << 8) | purpose, k.k0, k.k1);
+}
+
 // Uniform on (0, 1): ((r >> 9) + 1/2) 2^-23, exact in float and double.
 template <class V>
 __device__ __forceinline__ V u23(uint32_t r)

@@ -42,6 +42,8 @@ struct StepArgs {
     double c, fE;
     float c_f, fE_f;
     RngKey rng;
+    const uint64_t* step_dev;  // step index in device memory (null: rng.step); step = *step_dev + step_add
+    uint32_t step_add;
     const double* n97_f;   // N97 table (see mcc_device.cuh), double and float copies
     const double* n97_dh;
     const float* n97_f32;
@@ -72,6 +74,7 @@ void n97_table(double* f, double* dh);
 
 // Kernel launches (defined in mcc_cell.cu / mcc_bin.cu).
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_step_advance(uint64_t* step, uint64_t by, cudaStream_t st);
 cudaError_t launch_cell_order(const int64_t* offsets, int32_t n_cells, int32_t S, int32_t* order, cudaStream_t st);
 int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem);
 cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem);

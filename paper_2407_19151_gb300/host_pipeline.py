@@ -23,6 +23,8 @@ def step_host(vx, vy, vz, w, offsets, n_cells: int, n_species: int, species, lnL
               interactions=None):
     """Advance the host state (vx, vy, vz: pinned CPU tensors, float32 or float64; w: pinned float64) by n_steps
     in place. offsets: host int64 segment offsets. Returns the per-cell (corr_pairs, fail_count) as host arrays."""
+    if getattr(params, "step_device", None) is not None:
+        raise ValueError("step_host takes the step index from params.step (one call per step range)")
     dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
     off = np.asarray(offsets, dtype=np.int64)
     if max_cell is None:

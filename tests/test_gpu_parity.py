@@ -281,6 +281,37 @@ def test_fused_mixed_precision_options(mcc, name, make, kw, scatter_max):
     assert err[ok].max() < 2e-4
 
 
+def test_graph_of_one_step_serves_every_step(mcc):
+    """With the step index in device memory, a CUDA graph captured from one fused step, replayed three times, gives
+    exactly the three steps of a direct call, and leaves the counter three steps on."""
+    import torch
+    wl = W.three_species(n_cells=60, mean_count=90)
+    sp = _species(wl)
+    v0, w, off = device_state(wl, "f32")
+    v1 = [x.clone() for x in v0]
+    pp, _ = _params(mcc, wl, step=11)
+    mcc.mcc_step_fused(*v0, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, pp, n_steps=3)
+    counter = torch.tensor([0], dtype=torch.int64, device="cuda")
+    pd, _ = _params(mcc, wl, step=0)
+    pd.step_device = counter
+    warm = [x.clone() for x in v1]
+    mcc.mcc_step_fused(*warm, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, pd, n_steps=1,
+                       max_cell=int(wl.counts.sum(1).max()))  # workspaces, warm-up
+    torch.cuda.synchronize()
+    counter.fill_(11)
+    g = torch.cuda.CUDAGraph()
+    mc = int(wl.counts.sum(1).max())  # given, so that the captured call does no host read
+    with torch.cuda.graph(g):
+        mcc.mcc_step_fused(*v1, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, pd, n_steps=1, max_cell=mc)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    mcc.sync_status(0)
+    assert int(counter.item()) == 14
+    for a, b in zip(v0, v1):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
 def test_fused_slab_path_matches_tile(mcc):
     """Cells larger than the on-chip tile run from the workspace slabs and give the same result."""
     wl = W.three_species(n_cells=40, mean_count=300, precision="f64")
