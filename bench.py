@@ -21,6 +21,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -104,7 +105,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+        out_dir = os.environ.get("MCC_BENCH_OUT") or os.path.join(tempfile.gettempdir(), "mcc_bench")
+        self.path = os.path.join(out_dir, f"clocks_bench_{index}.csv")
 
     def __enter__(self):
         try:
