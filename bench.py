@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-bin", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' step times")
     return ap.parse_args()
 
 
@@ -205,6 +206,45 @@ def run_reference(args):
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def configs_measure(dev, hbm):
+    """Step time of the other synthetic workloads (the paper's test plasmas at GPU sizes): isotropisation (FP64),
+    equilibration (mixed, TA77 and N97), relativistic beam (mixed). Fused steps, CUDA events, after two warm-up
+    steps; pairs/s and the HBM fraction of their algorithmic bytes."""
+    import torch
+
+    import paper_2407_19151_gb300 as mcc
+    from paper_2407_19151_gb300 import workloads as W
+    cases = [("isotropisation", W.isotropisation(), "f64"),
+             ("equilibration_ta77", W.equilibration(method=W.TA77), "f32"),
+             ("equilibration_n97", W.equilibration(method=W.N97), "f32"),
+             ("relativistic_beam", W.relativistic_beam(), "f32")]
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for name, wl, prec in cases:
+        dt_ = torch.float64 if prec == "f64" else torch.float32
+        v = [torch.tensor(np.asarray(x), dtype=dt_, device=dev) for x in (wl.vx, wl.vy, wl.vz)]
+        w = torch.from_numpy(wl.w).to(dev)
+        off = torch.from_numpy(wl.offsets).to(dev)
+        sp = list(zip(wl.q.tolist(), wl.m.tolist()))
+        mc = int(wl.counts.sum(axis=1).max())
+        p = mcc.Params(method=wl.method, relativistic=wl.relativistic, dt=wl.dt, fE=wl.fE, c=wl.c, seed=wl.seed)
+        mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, p, n_steps=2, max_cell=mc)
+        torch.cuda.synchronize(dev)
+        k = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p.step = 2
+        e0.record(stream)
+        mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, p, n_steps=k, max_cell=mc)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        mcc.sync_status(dev.index or 0)
+        ms = e0.elapsed_time(e1) / k
+        out[name] = {"precision": prec, "n_cells": wl.n_cells, "n_particles": wl.n, "ms_per_step": ms,
+                     "pairs_per_s": wl.pairs_per_step() / (ms * 1e-3),
+                     "hbm_frac": BYTES_PER_PARTICLE[prec] * wl.n / (ms * 1e-3) / 1e9 / hbm}
+    return out
 
 
 def bin_measure(wl, dev):
@@ -423,6 +463,7 @@ def run_ours(args):
         return
     adj = None if (args.no_adjoint or world > 1) else adjoint_measure(dev)
     binning = None if (args.no_bin or world > 1) else bin_measure(wl, dev)
+    other = None if (args.no_configs or world > 1) else configs_measure(dev, hbm)
     cb = None if (args.no_cpu or world > 1) else cpu_baseline(wl, one_thread=True)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -448,6 +489,7 @@ def run_ours(args):
         "fp64_step": fp64,
         "adjoint": adj,
         "binning": binning,
+        "other_workloads": other,
         "cpu_baseline": cb,
     }
     print(json.dumps(line), flush=True)
