@@ -90,6 +90,8 @@ def lib():
             "orc_philox4x32_10": (None, [u32, u32, u32]),
             "orc_bin": (C.c_int, [i32, i32, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
             "orc_set_threads": (None, [C.c_int32]),
+            "orc_push": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_int64, i32, d, C.c_double, C.c_int32, C.c_double, i32]),
             "orc_nxn_slot": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int64, i64, i64]),
             "orc_nxn_slots": (C.c_int64, [C.c_int64, C.c_int64, C.c_int32, i64]),
             "orc_bin_weighted": (C.c_int, [i32, i32, d, C.c_int64, C.c_int32, C.c_int32, i32, i64]),
@@ -153,6 +155,25 @@ def nxn_schedule(na: int, nb: int, intra: bool):
 def set_threads(n: int):
     """Host threads used by step() (timing only)."""
     lib().orc_set_threads(int(n))
+
+
+def push(x, y, z, vx, vy, vz, grid, dt: float, relativistic: bool = False, c: float = 1.0):
+    """Free-streaming push in a periodic box (see orc_push), in the precision of the given arrays (float64 or
+    float32, all alike). ``grid`` = ((nx, ny, nz), (lx, ly, lz)). Returns (x, y, z, cell) as new arrays."""
+    (nx, ny, nz), (lx, ly, lz) = grid
+    dt_ = np.asarray(vx).dtype
+    if dt_ not in (np.float64, np.float32):
+        raise TypeError("float64 or float32 arrays")
+    arrs = [np.array(a, dtype=dt_, copy=True) for a in (x, y, z)]
+    vel = [np.ascontiguousarray(a, dtype=dt_) for a in (vx, vy, vz)]
+    n = len(vel[0])
+    cell = np.zeros(n, dtype=np.int32)
+    nc = np.array([nx, ny, nz], dtype=np.int32)
+    l = np.array([lx, ly, lz], dtype=np.float64)
+    vp = [a.ctypes.data_as(C.c_void_p) for a in arrs + vel]
+    _check(lib().orc_push(0 if dt_ == np.float64 else 1, *vp, n, _p(nc, C.c_int32), _p(l, C.c_double), float(dt),
+                          int(bool(relativistic)), float(c), _p(cell, C.c_int32)), "push")
+    return arrs[0], arrs[1], arrs[2], cell
 
 
 def bin_particles(cell, species, n_cells: int, n_species: int):

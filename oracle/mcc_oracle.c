@@ -930,3 +930,71 @@ void orc_set_threads(int32_t n)
     (void)n;
 #endif
 }
+
+/* ---------------------------------------------------------------------------------------------- PIC coupling */
+
+/* Free-streaming push (Sec. 2, Eq. Boltzmann, left-hand side with a = 0): per axis x <- x + v dt, with
+ * v = u / gamma, gamma = sqrt(1 + |u|^2 / c^2) in relativistic mode; then the periodic image in [0, L) and the
+ * cell index floor(x nx / L). Written once per precision so that each operation rounds in that precision. */
+#define ORC_DEFINE_PUSH(T, SUF, SQRT, FLOOR)                                                                        \
+    static T orc_wrap_##SUF(T x, T L)                                                                            \
+    {                                                                                                            \
+        if (x >= (T)0 && x < L) return x;                                                                        \
+        T q = FLOOR(x / L);                                                                                      \
+        T r = x - q * L;                                                                                         \
+        if (r < (T)0) r = r + L;                                                                                 \
+        if (r >= L) r = r - L;                                                                                   \
+        if (!(r >= (T)0 && r < L)) r = (T)0; /* a non-finite position */                                         \
+        return r;                                                                                                \
+    }                                                                                                            \
+    static void orc_push_##SUF(T* x, T* y, T* z, const T* vx, const T* vy, const T* vz, int64_t n,              \
+                               const int32_t nc[3], const double l[3], double dt, int32_t rel, double c,         \
+                               int32_t* cell)                                                                    \
+    {                                                                                                            \
+        const T tdt = (T)dt, c2 = (T)(c * c);                                                                    \
+        T L[3], sx[3];                                                                                           \
+        for (int d = 0; d < 3; ++d) {                                                                            \
+            L[d] = (T)l[d];                                                                                      \
+            sx[d] = (T)((double)nc[d] / l[d]);                                                                   \
+        }                                                                                                        \
+        T* pos[3] = {x, y, z};                                                                                   \
+        for (int64_t i = 0; i < n; ++i) {                                                                        \
+            const T u[3] = {vx[i], vy[i], vz[i]};                                                                \
+            T ginv = (T)1;                                                                                       \
+            if (rel) {                                                                                           \
+                T s = u[0] * u[0];                                                                               \
+                s = s + u[1] * u[1];                                                                             \
+                s = s + u[2] * u[2];                                                                             \
+                ginv = (T)1 / SQRT((T)1 + s / c2);                                                               \
+            }                                                                                                    \
+            int32_t id[3];                                                                                       \
+            for (int d = 0; d < 3; ++d) {                                                                        \
+                const T v = rel ? u[d] * ginv : u[d];                                                            \
+                const T step = v * tdt;                                                                          \
+                const T p = orc_wrap_##SUF(pos[d][i] + step, L[d]);                                              \
+                pos[d][i] = p;                                                                                   \
+                const T t = p * sx[d];                                                                           \
+                int32_t k = (int32_t)FLOOR(t);                                                                   \
+                id[d] = k < nc[d] ? k : nc[d] - 1;                                                               \
+            }                                                                                                    \
+            cell[i] = id[0] + nc[0] * (id[1] + nc[1] * id[2]);                                                   \
+        }                                                                                                        \
+    }
+
+ORC_DEFINE_PUSH(double, f64, sqrt, floor)
+ORC_DEFINE_PUSH(float, f32, sqrtf, floorf)
+
+int orc_push(int32_t prec, void* x, void* y, void* z, const void* vx, const void* vy, const void* vz, int64_t n,
+             const int32_t nc[3], const double l[3], double dt, int32_t relativistic, double c, int32_t* cell)
+{
+    if (n < 0 || (prec != 0 && prec != 1)) return -1;
+    for (int d = 0; d < 3; ++d)
+        if (nc[d] < 1 || !(l[d] > 0.0)) return -1;
+    if (prec == 0)
+        orc_push_f64((double*)x, (double*)y, (double*)z, (const double*)vx, (const double*)vy, (const double*)vz, n,
+                     nc, l, dt, relativistic, c, cell);
+    else
+        orc_push_f32((float*)x, (float*)y, (float*)z, (const float*)vx, (const float*)vy, (const float*)vz, n, nc, l,
+                     dt, relativistic, c, cell);
+    return 0;
+}

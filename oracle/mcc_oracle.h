@@ -17,6 +17,8 @@
  *                          equilibration expectations computed by brute force over the N x N pairs.
  *   orc_correct            pinned: exact momentum/energy invariants, first-order limit Eqs. vp1_inelastic_2 /
  *                          vp2_inelastic_2, Test-1 closed-form equilibrium.
+ *   orc_push               pinned: exact dyadic displacements and wraps, cell ids against exact rational floors,
+ *                          relativistic displacements against 50-digit decimal arithmetic.
  *   relativistic pieces    pinned by invariants (4-momentum conservation, Eq. alpha_Eq0 residual, gamma->1 limit);
  *                          the relativistic scatter kinematics have no printed formula and are otherwise
  *                          "parity unpinned" beyond those invariants.
@@ -86,6 +88,13 @@ int orc_correct(double* vx, double* vy, double* vz, const double* w, const int64
                 const double* backup, int32_t* corr_pairs, int32_t* fail_flags);
 
 void orc_set_threads(int32_t n);
+
+/* Free-streaming push of PIC coupling (Sec. 2, Eq. Boltzmann: the left-hand side advances positions, here with
+ * a = 0) in a periodic box of nc[0] x nc[1] x nc[2] cells over [0, l[d]). prec 0: double positions and velocities,
+ * prec 1: float. Every operation in that precision, rounded, no fused multiply-add; constants rounded once from
+ * double (dt, l, c * c, nc / l). Positions updated in place; cell = ix + nx (iy + ny iz). */
+int orc_push(int32_t prec, void* x, void* y, void* z, const void* vx, const void* vy, const void* vz, int64_t n,
+             const int32_t nc[3], const double l[3], double dt, int32_t relativistic, double c, int32_t* cell);
 
 int orc_step(double* vx, double* vy, double* vz, const double* w, const int64_t* offsets, int32_t n_cells,
              int32_t n_species, const double* q, const double* m, const double* lnL, const int32_t* interactions,

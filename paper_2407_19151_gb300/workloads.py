@@ -263,6 +263,41 @@ def three_species(n_cells: int = 1 << 18, mean_count: float = 512.0, sigma: floa
                     n_steps=steps, seed=0x5EED0005)
 
 
+def grid_dims(n_cells: int) -> tuple[int, int, int]:
+    """A near-cubic nx x ny x nz factorisation of n_cells (64^3 for 2^18 cells)."""
+    n = int(n_cells)
+    nz = max(d for d in range(1, int(round(n ** (1.0 / 3.0))) + 1) if n % d == 0)
+    m = n // nz
+    ny = max(d for d in range(1, int(m ** 0.5) + 1) if m % d == 0)
+    return m // ny, ny, nz
+
+
+def pic_setup(wl: Workload, cfl: float = 0.25, data_seed: int = 4242):
+    """Positions for PIC coupling: the cells of ``wl`` on a periodic grid of unit cubes (volume dV = 1, cell id
+    ix + nx (iy + ny iz)), each particle uniform inside its own cell, in the workload's precision. The push time
+    step is set by a drift Courant number: ``cfl`` cell widths per step for the thermal speed of the lightest species
+    (for a relativistic workload, for c), so that a fraction of the particles changes cell every step. Returns
+    (grid, x, y, z, dt_push) with grid = ((nx, ny, nz), (lx, ly, lz))."""
+    rng = np.random.default_rng(data_seed)
+    nx, ny, nz = grid_dims(wl.n_cells)
+    cell = wl.cell_of_particles().astype(np.int64)
+    idx = (cell % nx, (cell // nx) % ny, cell // (nx * ny))
+    dtype = np.float32 if wl.precision == "f32" else np.float64
+    pos = []
+    for i in idx:
+        p = (i + rng.random(wl.n)).astype(dtype)
+        top = np.nextafter((i + 1).astype(dtype), dtype(0))
+        pos.append(np.minimum(p, top))   # rounding must not carry a particle into the next cell
+    if wl.relativistic:
+        v_t = wl.c
+    else:
+        light = int(np.argmin(wl.m))
+        sp = wl.species_of_particles()
+        v_t = float(np.sqrt(np.mean(np.asarray(wl.vx, dtype=np.float64)[sp == light] ** 2)))
+    grid = ((nx, ny, nz), (float(nx), float(ny), float(nz)))
+    return grid, pos[0], pos[1], pos[2], cfl / v_t
+
+
 CONFIGS = {
     1: isotropisation,
     2: equilibration,
