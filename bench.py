@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-bin", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' step times")
+    ap.add_argument("--no-pic", action="store_true", help="skip the PIC-coupling (push, re-bin, step) timing")
     return ap.parse_args()
 
 
@@ -288,6 +289,73 @@ def bin_measure(wl, dev):
     return res
 
 
+def pic_measure(wl, dev, hbm, steps: int = 4):
+    """PIC coupling on the same particles (row f3): positions in 64^3 unit cells (periodic), and per step the
+    free-streaming push (drift Courant number 0.25 for the electrons' thermal speed), the re-bin (stable, or with
+    segments by descending weight), one gather pass of the eight particle arrays, and the collision step. Each phase
+    timed with CUDA events on the stream, after one untimed step; the re-bin is now a per-step cost."""
+    import dataclasses
+
+    import torch
+
+    import paper_2407_19151_gb300 as mcc
+    from paper_2407_19151_gb300 import workloads as W
+    C, S = wl.n_cells, wl.n_species
+    grid, x, y, z, dt_push = W.pic_setup(wl, cfl=0.25)
+    sp = wl.species_of_particles()
+    species = list(zip(wl.q.tolist(), wl.m.tolist()))
+    stream = torch.cuda.current_stream(dev)
+    out = {"grid": list(grid[0]), "cfl": 0.25, "dt_push": dt_push, "particles": wl.n}
+    for order in ("weight", "stable"):
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        arrays = [to(x), to(y), to(z), to(wl.vx), to(wl.vy), to(wl.vz), to(wl.w), to(sp)]
+        spare = [torch.empty_like(a) for a in arrays]
+        cell = torch.empty(wl.n, dtype=torch.int32, device=dev)
+        off = torch.from_numpy(wl.offsets).to(dev)
+        p = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=5000)
+        tot = {"push": 0.0, "bin": 0.0, "gather": 0.0, "step": 0.0}
+        moved = 0.0
+        pairs = 0
+        for k in range(steps + 1):
+            before = torch.repeat_interleave(torch.arange(C, device=dev, dtype=torch.int32),
+                                             off[S::S] - off[:-1:S], output_size=wl.n)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            ev[0].record(stream)
+            mcc.mcc_push(*arrays[:6], grid, dt_push, cell=cell)
+            ev[1].record(stream)
+            if order == "weight":
+                perm, off = mcc.mcc_bin_weighted(cell, arrays[7], arrays[6], C, S)
+            else:
+                perm, off = mcc.mcc_bin(cell, arrays[7], C, S)
+            ev[2].record(stream)
+            mcc.mcc_gather_n(arrays, perm, outs=spare)
+            ev[3].record(stream)
+            arrays, spare = spare, arrays
+            moved = float((cell != before).float().mean().item())
+            counts = (off[1:] - off[:-1]).view(C, S).cpu().numpy()
+            mc = int(counts.sum(axis=1).max())
+            ev[4].record(stream)
+            mcc.mcc_step_fused(*arrays[3:7], off, C, S, species, wl.lnL, dataclasses.replace(p, step=5000 + k),
+                               n_steps=1, max_cell=mc)
+            ev[5].record(stream)
+            torch.cuda.synchronize(dev)
+            if k > 0:
+                for name, a, b in (("push", 0, 1), ("bin", 1, 2), ("gather", 2, 3), ("step", 4, 5)):
+                    tot[name] += ev[a].elapsed_time(ev[b]) / steps
+                pairs += dataclasses.replace(wl, counts=counts).pairs_per_step() / steps
+        mcc.sync_status(dev.index or 0)
+        ms = sum(tot.values())
+        out[order] = {"ms_per_step": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                      **{f"{k}_ms": v for k, v in tot.items()}, "moved_fraction": moved,
+                      "push_hbm_frac": 40 * wl.n / (tot["push"] * 1e-3) / 1e9 / hbm,
+                      "gather_hbm_frac": 76 * wl.n / (tot["gather"] * 1e-3) / 1e9 / hbm}
+        del arrays, spare, cell, perm, off
+    out["note"] = ("push 40 B and gather 76 B of algorithmic traffic per particle (float positions and velocities); "
+                   "'weight': re-bin with segments by descending weight (the step skips its weight sort); "
+                   "'stable': plain stable re-bin")
+    return out
+
+
 def adjoint_measure(dev):
     """Differentiable step (1024 cells x 512 particles, two species of mass ratio 1836, FP64, N97): 50 steps with a
     checkpoint every 10, gradient of the final per-species temperatures and drifts with respect to the initial
@@ -464,6 +532,7 @@ def run_ours(args):
     adj = None if (args.no_adjoint or world > 1) else adjoint_measure(dev)
     binning = None if (args.no_bin or world > 1) else bin_measure(wl, dev)
     other = None if (args.no_configs or world > 1) else configs_measure(dev, hbm)
+    pic = None if (args.no_pic or world > 1) else pic_measure(wl, dev, hbm)
     cb = None if (args.no_cpu or world > 1) else cpu_baseline(wl, one_thread=True)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -490,6 +559,7 @@ def run_ours(args):
         "adjoint": adj,
         "binning": binning,
         "other_workloads": other,
+        "pic_coupling": pic,
         "cpu_baseline": cb,
     }
     print(json.dumps(line), flush=True)

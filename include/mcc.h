@@ -192,6 +192,44 @@ int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32
 /* Gather a double or float array through perm: out[k] = in[perm[k]] (elem_bytes 4 or 8). */
 int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream);
 
+/* mcc_gather for up to MCC_MAX_GATHER arrays in one pass over perm: out[a][k] = in[a][perm[k]].
+ *   in, out, elem_bytes   host arrays of n_arrays entries (device pointers; elem_bytes 4 or 8 each); in[a] and
+ *                         out[a] must not overlap
+ *   n_arrays              1 .. MCC_MAX_GATHER */
+#define MCC_MAX_GATHER 8
+int mcc_gather_n(const void* const* in, void* const* out, const int32_t* elem_bytes, int32_t n_arrays,
+                 const int32_t* perm, int64_t n, mcc_stream stream);
+
+/*
+ * Particle push for PIC coupling. The collision operator is the right-hand side of the Boltzmann equation
+ * (Sec. 2, Eq. Boltzmann); a particle-in-cell code advances positions by the left-hand side between collision
+ * steps, and the particles then have to be re-binned (mcc_bin) before the next step. mcc_push is the free-streaming
+ * part of that advance (the acceleration a = 0): x <- x + v dt per axis, v = u / gamma with
+ * gamma = sqrt(1 + |u|^2 / c^2) in relativistic mode (u the stored proper velocity), in a periodic box, and it writes
+ * each particle's new cell id for mcc_bin.
+ *
+ * The grid: nx x ny x nz cells over the box [0, lx) x [0, ly) x [0, lz); cell id = ix + nx * (iy + ny * iz).
+ * Arithmetic, in the precision T of the positions (double for MCC_F64, float for MCC_F32_MIXED), every operation
+ * rounded to nearest with no fused multiply-add, constants rounded once from double to T: dt, L = l, c2 = c * c
+ * (product in double) and sx = nx / lx (quotient in double):
+ *   gamma_inv = 1 / sqrt(1 + ((ux*ux + uy*uy) + uz*uz) / c2)   (relativistic; 1 otherwise)
+ *   x' = x + (u * gamma_inv) * dt                               (non-relativistic: x + u * dt)
+ *   if x' is outside [0, L): r = x' - floor(x' / L) * L; if r < 0, r = r + L; if r >= L, r = r - L; a result
+ *   still outside [0, L) (a non-finite x') becomes 0
+ *   ix = (int)(x' * sx), at most nx - 1
+ * so a host program doing the same operations in T gets the same positions and cell ids bit for bit.
+ *   P            velocities (P->prec selects T) and n; P->w is not read
+ *   x, y, z      [n] device T: positions in the box, updated in place
+ *   cell_out     [n] device int32: the new cell ids
+ *   nx, ny, nz   >= 1, nx * ny * nz <= INT32_MAX; lx, ly, lz > 0 and finite; dt finite; c > 0 if relativistic
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    double lx, ly, lz;
+} mcc_grid;
+int mcc_push(const mcc_particles* P, void* x, void* y, void* z, const mcc_grid* grid, double dt,
+             int32_t relativistic, double c, int32_t* cell_out, mcc_stream stream);
+
 /*
  * mcc_pair: random binary pairs of Takizuka-Abe for interaction `inter` between species sa <= sb
  * (Sec. 3.2, Fig. TApairing; Algorithm 1, second step).

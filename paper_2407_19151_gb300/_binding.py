@@ -35,6 +35,11 @@ class _Particles(C.Structure):
                 ("n", C.c_int64), ("prec", C.c_int32)]
 
 
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("lx", C.c_double), ("ly", C.c_double),
+                ("lz", C.c_double)]
+
+
 class _Params(C.Structure):
     _fields_ = [("method", C.c_int32), ("relativistic", C.c_int32), ("dt", C.c_double), ("dV", C.c_double),
                 ("eps0", C.c_double), ("c", C.c_double), ("fE", C.c_double), ("sort_by_weight", C.c_int32),
@@ -99,6 +104,8 @@ def lib():
         "mcc_bin_weighted": (C.c_int, [vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t,
                                        vp]),
         "mcc_gather": (C.c_int, [vp, vp, C.c_int64, C.c_int32, vp, vp]),
+        "mcc_gather_n": (C.c_int, [P(vp), P(vp), P(C.c_int32), C.c_int32, vp, C.c_int64, vp]),
+        "mcc_push": (C.c_int, [P(_Particles), vp, vp, vp, P(_Grid), C.c_double, C.c_int32, C.c_double, vp, vp]),
         "mcc_bin_static": (C.c_int, [vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp]),
         "mcc_pair": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                C.c_uint64, vp, vp, vp, vp]),
@@ -267,6 +274,48 @@ def mcc_gather(x: torch.Tensor, perm: torch.Tensor, stream=None) -> torch.Tensor
     _check(lib().mcc_gather(_ptr(x), _ptr(perm), x.numel(), x.element_size(), _ptr(out),
                             _stream(stream, x.device)), "mcc_gather")
     return out
+
+
+def mcc_gather_n(xs, perm: torch.Tensor, outs=None, stream=None):
+    """One pass over perm for up to 8 arrays: outs[a][k] = xs[a][perm[k]]. Returns the outputs (allocated if not
+    given)."""
+    xs = list(xs)
+    if outs is None:
+        outs = [torch.empty_like(x) for x in xs]
+    n = perm.numel()
+    for x, o in zip(xs, outs):
+        if x.numel() != n or o.numel() != n or x.element_size() != o.element_size() or not x.is_contiguous() \
+                or not o.is_contiguous():
+            raise ValueError("every array and output must be contiguous with one element per permutation entry")
+    k = len(xs)
+    ins = (C.c_void_p * k)(*[x.data_ptr() for x in xs])
+    ous = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+    eb = (C.c_int32 * k)(*[x.element_size() for x in xs])
+    _check(lib().mcc_gather_n(ins, ous, eb, k, _ptr(perm), n, _stream(stream, perm.device)), "mcc_gather_n")
+    return outs
+
+
+def mcc_push(x, y, z, vx, vy, vz, grid, dt: float, relativistic: bool = False, c: float = 1.0, cell=None,
+             stream=None) -> torch.Tensor:
+    """Free-streaming push in a periodic box, positions updated in place (same dtype as the velocities); returns the
+    new cell ids (int32). ``grid`` = ((nx, ny, nz), (lx, ly, lz))."""
+    (nx, ny, nz), (lx, ly, lz) = grid
+    for t in (x, y, z):
+        if t.dtype != vx.dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != vx.numel():
+            raise TypeError("positions must be contiguous CUDA tensors of the velocities' dtype and length")
+    if vx.dtype not in (torch.float64, torch.float32):
+        raise TypeError("velocities must be float64 or float32")
+    for t in (vx, vy, vz):
+        if t.dtype != vx.dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != vx.numel():
+            raise TypeError("vx, vy, vz must be contiguous CUDA tensors of one dtype and length")
+    P = _Particles(vx.data_ptr(), vy.data_ptr(), vz.data_ptr(), None, vx.numel(),
+                   F64 if vx.dtype == torch.float64 else F32_MIXED)  # the push reads no weights
+    if cell is None:
+        cell = torch.empty(vx.numel(), dtype=torch.int32, device=vx.device)
+    g = _Grid(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz))
+    _check(lib().mcc_push(C.byref(P), _ptr(x), _ptr(y), _ptr(z), C.byref(g), float(dt), int(bool(relativistic)),
+                          float(c), _ptr(cell), _stream(stream, vx.device)), "mcc_push")
+    return cell
 
 
 def mcc_pair(offsets: torch.Tensor, n_cells: int, n_species: int, sa: int, sb: int, inter: int, seed: int,

@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu", "mcc_adjoint.cu"]
-HEADERS = ["mcc_device.cuh", "mcc_kernels.h"]
+SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu", "mcc_adjoint.cu", "mcc_pic.cu"]
+HEADERS = ["mcc_device.cuh", "mcc_kernels.h", "mcc_pic.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -6,6 +6,7 @@
 
 #include "../../include/mcc.h"
 #include "mcc_kernels.h"
+#include "mcc_pic.h"
 
 struct mcc_ctx {
     int device;
@@ -350,6 +351,43 @@ int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_byte
 {
     if (n < 0 || (elem_bytes != 4 && elem_bytes != 8) || (n > 0 && (!in || !perm || !out))) return MCC_ERR_INVALID_ARG;
     return cuda_status(mcc::launch_gather(in, perm, n, elem_bytes, out, S(stream)));
+}
+
+int mcc_gather_n(const void* const* in, void* const* out, const int32_t* elem_bytes, int32_t n_arrays,
+                 const int32_t* perm, int64_t n, mcc_stream stream)
+{
+    if (n < 0 || n_arrays < 1 || n_arrays > MCC_MAX_GATHER || !in || !out || !elem_bytes) return MCC_ERR_INVALID_ARG;
+    for (int j = 0; j < n_arrays; ++j) {
+        if (elem_bytes[j] != 4 && elem_bytes[j] != 8) return MCC_ERR_INVALID_ARG;
+        if (n > 0 && (!in[j] || !out[j])) return MCC_ERR_INVALID_ARG;
+    }
+    if (n > 0 && !perm) return MCC_ERR_INVALID_ARG;
+    return cuda_status(mcc::launch_gather_n(in, out, elem_bytes, n_arrays, perm, n, S(stream)));
+}
+
+int mcc_push(const mcc_particles* P, void* x, void* y, void* z, const mcc_grid* grid, double dt,
+             int32_t relativistic, double c, int32_t* cell_out, mcc_stream stream)
+{
+    if (!P || !grid || P->n < 0 || (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED)) return MCC_ERR_INVALID_ARG;
+    if (relativistic != 0 && relativistic != 1) return MCC_ERR_INVALID_ARG;
+    const int32_t nc[3] = {grid->nx, grid->ny, grid->nz};
+    const double l[3] = {grid->lx, grid->ly, grid->lz};
+    int64_t cells = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (nc[d] < 1 || !(l[d] > 0.0) || !std::isfinite(l[d])) return MCC_ERR_INVALID_ARG;
+        cells *= nc[d];
+        if (cells > INT32_MAX) return MCC_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(dt) || (relativistic && !(c > 0.0 && std::isfinite(c)))) return MCC_ERR_INVALID_ARG;
+    if (P->n == 0) return MCC_OK;
+    if (!P->vx || !P->vy || !P->vz || !x || !y || !z || !cell_out) return MCC_ERR_INVALID_ARG;
+    mcc::PushGrid g;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = nc[d];
+        g.l[d] = l[d];
+    }
+    return cuda_status(mcc::launch_push(P->prec == MCC_F32_MIXED, relativistic != 0, x, y, z, P->vx, P->vy, P->vz,
+                                        P->n, g, dt, c, cell_out, S(stream)));
 }
 
 int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_species, int32_t sa, int32_t sb,
