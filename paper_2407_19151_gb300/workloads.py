@@ -101,7 +101,13 @@ class Workload:
         their order): the layout in which the optional weight order of the energy correction is the identity."""
         off = self.offsets
         seg = np.repeat(np.arange(len(off) - 1, dtype=np.int64), np.diff(off))
-        order = np.lexsort((np.arange(self.n, dtype=np.int64), -self.w, seg))
+        # by segment, then descending weight, then index: a stable sort by weight, then a stable sort by segment.
+        # Positive doubles order like their IEEE bit patterns read as int64, so both sorts are integer sorts (torch's
+        # stable integer sort on the host is a radix sort, ~10x faster than numpy's at 1e8 particles).
+        import torch
+        by_w = torch.sort(torch.from_numpy(-np.ascontiguousarray(self.w).view(np.int64)), stable=True).indices
+        seg_t = torch.from_numpy(seg)[by_w]
+        order = by_w[torch.sort(seg_t, stable=True).indices].numpy()
         return Workload(self.name, self.n_cells, self.q, self.m, self.lnL, self.counts.copy(), self.vx[order],
                         self.vy[order], self.vz[order], self.w[order], self.dt, self.method, self.relativistic,
                         self.fE, self.precision, self.n_steps, self.seed, self.dV, self.eps0, self.c,

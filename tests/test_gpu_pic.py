@@ -82,24 +82,14 @@ def test_gather_n_exact(mcc, n):
         np.testing.assert_array_equal(o.cpu().numpy(), a[perm])
 
 
-def _loop_pair(mcc, wl, dtype, n_steps, cfl=0.5, order="stable"):
-    """The PicLoop on the GPU and the same push / bin / gather / step sequence through the oracle."""
-    import torch
+def _oracle_loop(wl, dtype, n_steps, cfl=0.5, order="stable", v0=None):
+    """The push / bin / gather / step sequence through the oracle: positions and velocities stored in the given
+    precision for the push, FP64 for the collision step."""
     grid, x, y, z, dt_push = W.pic_setup(wl, cfl=cfl)
-    tdt = torch.float64 if dtype == "f64" else torch.float32
     npdt = np.float64 if dtype == "f64" else np.float32
     sp = wl.species_of_particles()
-    v = [np.asarray(a, dtype=npdt) for a in (wl.vx, wl.vy, wl.vz)]
+    v = [np.asarray(a, dtype=npdt) for a in (v0 if v0 is not None else (wl.vx, wl.vy, wl.vz))]
     pos = [np.asarray(a, dtype=npdt) for a in (x, y, z)]
-    base = dict(method=wl.method, relativistic=wl.relativistic, dt=wl.dt, dV=wl.dV, eps0=wl.eps0, c=wl.c, fE=wl.fE,
-                seed=wl.seed, step=3)
-    loop = mcc.PicLoop(*[_t(a) for a in pos], *[_t(a).to(tdt) for a in v], _t(wl.w), _t(sp), _t(wl.offsets),
-                       wl.n_cells, wl.n_species, grid, list(zip(wl.q.tolist(), wl.m.tolist())), wl.lnL,
-                       mcc.Params(**base), dt_push, order=order)
-    _, fail = loop.step(n_steps)
-    mcc.sync_status(0)
-    got = [a.cpu().numpy() for a in loop.state]
-    # oracle: positions and velocities in the same storage precision for the push, FP64 for the collision step
     w, s = wl.w.copy(), sp.copy()
     for t in range(n_steps):
         xo, yo, zo, cell = O.push(*pos, *v, grid, dt_push, relativistic=wl.relativistic, c=wl.c)
@@ -109,11 +99,35 @@ def _loop_pair(mcc, wl, dtype, n_steps, cfl=0.5, order="stable"):
         v = [a[perm] for a in v]
         w, s = w[perm], s[perm]
         st = O.State(*[a.astype(np.float64) for a in v], w, off, wl.n_cells, wl.n_species)
-        _, rf = O.step(st, wl.q, wl.m, wl.lnL, O.Params(**dict(base, step=3 + t)), n_steps=1)
+        _, rf = O.step(st, wl.q, wl.m, wl.lnL, O.Params(**dict(_base(wl), step=3 + t)), n_steps=1)
         vv = st.v()
         v = [vv[:, d].astype(npdt) for d in range(3)]
+    return pos, v, w, s, off, st.v(), rf
+
+
+def _base(wl):
+    return dict(method=wl.method, relativistic=wl.relativistic, dt=wl.dt, dV=wl.dV, eps0=wl.eps0, c=wl.c, fE=wl.fE,
+                seed=wl.seed, step=3)
+
+
+def _loop_pair(mcc, wl, dtype, n_steps, cfl=0.5, order="stable"):
+    """The PicLoop on the GPU and the same sequence through the oracle."""
+    import torch
+    grid, x, y, z, dt_push = W.pic_setup(wl, cfl=cfl)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    npdt = np.float64 if dtype == "f64" else np.float32
+    sp = wl.species_of_particles()
+    v = [np.asarray(a, dtype=npdt) for a in (wl.vx, wl.vy, wl.vz)]
+    pos = [np.asarray(a, dtype=npdt) for a in (x, y, z)]
+    loop = mcc.PicLoop(*[_t(a) for a in pos], *[_t(a).to(tdt) for a in v], _t(wl.w), _t(sp), _t(wl.offsets),
+                       wl.n_cells, wl.n_species, grid, list(zip(wl.q.tolist(), wl.m.tolist())), wl.lnL,
+                       mcc.Params(**_base(wl)), dt_push, order=order)
+    _, fail = loop.step(n_steps)
+    mcc.sync_status(0)
+    got = [a.cpu().numpy() for a in loop.state]
+    pos, v, w, s, off, vref, rf = _oracle_loop(wl, dtype, n_steps, cfl, order)
     ok = np.repeat(fail.cpu().numpy() == rf, np.diff(off[::wl.n_species]))  # last step's cells, same failures
-    return got, loop.offsets.cpu().numpy(), (pos, v, w, s, off, st.v()), ok
+    return got, loop.offsets.cpu().numpy(), (pos, v, w, s, off, vref), ok
 
 
 @pytest.mark.parametrize("order", ["stable", "weight"])
@@ -132,12 +146,22 @@ def test_pic_loop_fp64(mcc, order):
 
 
 def test_pic_loop_relativistic_fp64(mcc):
+    """Two relativistic push / re-bin / collision steps, FP64. Re-binning gathers, in some cells, a few co-moving
+    fast beam particles whose energy-correction pair is ill-conditioned: the oracle itself moves by ~2e-12 when its
+    inputs change by one ulp. Bound: 99.9% of particles within 1e-12, every particle within four times the oracle's
+    own one-ulp sensitivity (measured here) or 1e-12, whichever is larger."""
     wl = W.relativistic_beam(n_cells=60, count_lo=16, count_hi=200, precision="f64")
     got, off, (pos, v, w, s, roff, vref), ok = _loop_pair(mcc, wl, "f64", 2)
     np.testing.assert_array_equal(off, roff)
     np.testing.assert_array_equal(got[7], s)
+    rng = np.random.default_rng(0)
+    v1 = [np.asarray(a, np.float64) * (1 + rng.choice([-1.0, 1.0], wl.n) * 2.0 ** -52) for a in (wl.vx, wl.vy, wl.vz)]
+    *_, off1, vref1, _ = _oracle_loop(wl, "f64", 2, v0=v1)
+    np.testing.assert_array_equal(off1, roff)
+    sens = velocity_error(vref1, vref, roff).max()
     err = velocity_error(np.stack(got[3:6], axis=1), vref, roff)
-    assert err.max() < F64_TOL, err.max()
+    assert np.quantile(err, 0.999) < F64_TOL, np.quantile(err, 0.999)
+    assert err.max() < max(F64_TOL, 4 * sens), (err.max(), sens)
 
 
 def test_pic_loop_mixed(mcc):
