@@ -3,7 +3,9 @@
 //
 // histogram (atomic counts) -> exclusive scan -> scatter with atomic cursors (order within a segment arbitrary)
 // -> per-segment sort of the particle indices, which restores the stable (index) order. The result does not depend
-// on the order in which the atomics were served.
+// on the order in which the atomics were served. The atomics are warp-aggregated (lanes with equal keys add once),
+// which matters for nearly binned input such as a re-bin after a particle push; segments of up to 512 entries are
+// sorted by one warp in registers, larger ones by a whole CTA.
 #include <mutex>
 
 #include "mcc_kernels.h"
@@ -22,16 +24,31 @@ constexpr int kScanThreads = 1024;
 constexpr int kSegCap = 12288;  // indices sorted in shared memory per segment; larger segments sort in place
 constexpr int kSegCapW = 4096;  // weight-order keys sorted in shared memory per segment; larger ones in the workspace
 
+constexpr int kWarpSeg = 512;  // segments up to this size are sorted by one warp in registers
+
+// Key of particle i (cell * S + species), or -1 past the end or out of range (latched).
+__device__ __forceinline__ long long bin_key(const int32_t* __restrict__ cell, const int32_t* __restrict__ species,
+                                             int64_t i, int64_t n, int32_t n_cells, int32_t S, int32_t* status)
+{
+    if (i >= n) return -1;
+    const int32_t c = cell[i], s = species[i];
+    if (c < 0 || c >= n_cells || s < 0 || s >= S) {
+        if (status) latch(status, kErrBounds);
+        return -1;
+    }
+    return (long long)c * S + s;
+}
+
+// All lanes of a warp run the same trips (the loop index is the warp's base), so the match below sees the full warp.
 __global__ void k_hist(const int32_t* __restrict__ cell, const int32_t* __restrict__ species, int64_t n,
                        int32_t n_cells, int32_t S, int32_t* __restrict__ counts, int32_t* status)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = cell[i], s = species[i];
-        if (c < 0 || c >= n_cells || s < 0 || s >= S) {
-            latch(status, kErrBounds);
-            continue;
-        }
-        atomicAdd(&counts[(int64_t)c * S + s], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const long long key = bin_key(cell, species, base + lane, n, n_cells, S, status);
+        const unsigned m = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&counts[key], __popc(m));
     }
 }
 
@@ -70,11 +87,93 @@ __global__ void k_scatter(const int32_t* __restrict__ cell, const int32_t* __res
                           int32_t n_cells, int32_t S, const int64_t* __restrict__ offsets,
                           int32_t* __restrict__ cursor, int32_t* __restrict__ perm)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = cell[i], s = species[i];
-        if (c < 0 || c >= n_cells || s < 0 || s >= S) continue;
-        const int64_t key = (int64_t)c * S + s;
-        perm[offsets[key] + atomicAdd(&cursor[key], 1)] = (int32_t)i;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const long long key = bin_key(cell, species, base + lane, n, n_cells, S, nullptr);
+        const unsigned m = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(m) - 1;
+        int32_t at = 0;
+        if (key >= 0 && lane == leader) at = atomicAdd(&cursor[key], __popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (key >= 0) perm[offsets[key] + at + __popc(m & ((1u << lane) - 1u))] = (int32_t)(base + lane);
+    }
+}
+
+// One warp per segment of 2 .. kWarpSeg entries: the segment's indices in registers (K per lane), bitonic sort.
+// Every lane loads before the network's first shuffle and stores after its last, so the sort may run in place.
+template <int K>
+__device__ __noinline__ void warp_sort_seg_i32(int32_t* p, int n)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t x[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        x[r] = pos < n ? (uint64_t)(uint32_t)p[pos] : ~0ull;
+    }
+    warp_bitonic<K>(x);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        if (pos < n) p[pos] = (int32_t)(uint32_t)x[r];
+    }
+}
+
+// The weight order of one segment of 2 .. kWarpSeg entries (already in index order) by one warp: keys
+// weight_key(w, rank) sorted in registers, then each slot takes the index its key's rank points to; all reads of
+// the segment finish (warp barrier) before the first write.
+template <int K>
+__device__ __noinline__ void warp_sort_seg_w(const double* __restrict__ w, int32_t* p, int n)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t x[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        x[r] = pos < n ? weight_key(w[p[pos]], (uint32_t)pos) : ~0ull;
+    }
+    warp_bitonic<K>(x);
+    int32_t v[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        const int src = (int)(x[r] & kPermMask);
+        v[r] = pos < n ? p[src < n ? src : pos] : 0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        if (pos < n) p[pos] = v[r];
+    }
+}
+
+// Small segments, one warp each (the loop index is warp-uniform, so whole warps take the same branches).
+__global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __restrict__ offsets, int64_t nk,
+                                                              const double* __restrict__ w, int32_t* __restrict__ perm)
+{
+    const int64_t warp = ((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBinThreads) >> 5;
+    for (int64_t seg = warp; seg < nk; seg += nwarps) {
+        const int64_t b = offsets[seg];
+        const int n = (int)(offsets[seg + 1] - b);
+        if (n < 2 || n > kWarpSeg) continue;
+        int32_t* p = perm + b;
+        if (w == nullptr) {
+            if (n <= 32) warp_sort_seg_i32<1>(p, n);
+            else if (n <= 64) warp_sort_seg_i32<2>(p, n);
+            else if (n <= 128) warp_sort_seg_i32<4>(p, n);
+            else if (n <= 256) warp_sort_seg_i32<8>(p, n);
+            else warp_sort_seg_i32<16>(p, n);
+        } else {
+            if (n <= 32) warp_sort_seg_w<1>(w, p, n);
+            else if (n <= 64) warp_sort_seg_w<2>(w, p, n);
+            else if (n <= 128) warp_sort_seg_w<4>(w, p, n);
+            else if (n <= 256) warp_sort_seg_w<8>(w, p, n);
+            else warp_sort_seg_w<16>(w, p, n);
+        }
     }
 }
 
@@ -85,7 +184,7 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort(const int64_t* __restri
     for (int64_t seg = blockIdx.x; seg < nk; seg += gridDim.x) {
         const int64_t b = offsets[seg];
         const int n = (int)(offsets[seg + 1] - b);
-        if (n < 2) continue;
+        if (n <= kWarpSeg) continue;  // sorted by k_segsort_warp
         if (n <= kSegCap) {
             for (int i = threadIdx.x; i < n; i += kBinThreads) buf[i] = perm[b + i];
             __syncthreads();
@@ -110,7 +209,7 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort_w(const int64_t* __rest
     for (int64_t seg = blockIdx.x; seg < nk; seg += gridDim.x) {
         const int64_t b = offsets[seg];
         const int n = (int)(offsets[seg + 1] - b);
-        if (n < 2) continue;
+        if (n <= kWarpSeg) continue;  // ordered by k_segsort_warp
         uint64_t* k = n <= kSegCapW ? buf : keys + b;
         for (int i = threadIdx.x; i < n; i += kBinThreads) k[i] = weight_key(w[perm[b + i]], (uint32_t)i);
         __syncthreads();
@@ -164,9 +263,10 @@ cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, i
     k_scan<<<1, kScanThreads, 0, st>>>(counts, nk, offsets, status);
     if (n > 0) {
         k_scatter<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, offsets, cursor, perm);
+        k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, nullptr, perm);
         const int gs = grid_for(nk * kBinThreads, kBinThreads);
         k_segsort<<<gs, kBinThreads, 0, st>>>(offsets, nk, perm);
-        *launches += 3;
+        *launches += 4;
     }
     *launches += 1;
     return cudaGetLastError();
@@ -185,9 +285,10 @@ cudaError_t launch_bin_weighted(const int32_t* cell, const int32_t* species, con
     cudaError_t e = launch_bin(cell, species, n, n_cells, n_species, perm, offsets, ws, status, st, launches);
     if (e != cudaSuccess || n == 0) return e;
     uint64_t* keys = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + bin_workspace_bytes(n, nk));
+    k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm);
     const int gs = grid_for(nk * kBinThreads, kBinThreads);
     k_segsort_w<<<gs, kBinThreads, 0, st>>>(offsets, nk, w, perm, keys);
-    *launches += 1;
+    *launches += 2;
     return cudaGetLastError();
 }
 

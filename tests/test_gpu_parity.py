@@ -36,7 +36,11 @@ def _params(mcc, wl, **kw):
 
 
 # ------------------------------------------------------------------------------------------------- binning
-@pytest.mark.parametrize("n,C,S", [(0, 4, 2), (1, 1, 1), (1000, 7, 3), (200_000, 4096, 2), (30_000, 3, 1)])
+# segment sizes: ~50 and ~24 (one warp per segment), ~625 (one CTA, shared memory), ~30000 (one CTA, in place)
+BIN_CASES = [(0, 4, 2), (1, 1, 1), (1000, 7, 3), (200_000, 4096, 2), (20_000, 16, 2), (30_000, 3, 1)]
+
+
+@pytest.mark.parametrize("n,C,S", BIN_CASES)
 def test_bin_bit_exact(mcc, n, C, S):
     import torch
     rng = np.random.default_rng(n + C)
@@ -53,7 +57,7 @@ def test_bin_bit_exact(mcc, n, C, S):
     np.testing.assert_array_equal(perm.cpu().numpy(), rperm)
 
 
-@pytest.mark.parametrize("n,C,S", [(0, 4, 2), (1, 1, 1), (1000, 7, 3), (200_000, 4096, 2), (30_000, 3, 1)])
+@pytest.mark.parametrize("n,C,S", BIN_CASES)
 def test_bin_weighted_bit_exact(mcc, n, C, S):
     """Weight-ordered segments: exact ties, ties below the key width, distinct weights just above it; one case
     holds a segment of ~30k particles (keys sorted in the workspace instead of shared memory)."""
