@@ -5,7 +5,7 @@
 // -> per-segment sort of the particle indices, which restores the stable (index) order. The result does not depend
 // on the order in which the atomics were served. The atomics are warp-aggregated (lanes with equal keys add once),
 // which matters for nearly binned input such as a re-bin after a particle push; segments of up to 512 entries are
-// sorted by one warp in registers, larger ones by a whole CTA.
+// sorted by one warp in its slice of shared memory (warp barriers only), larger ones by a whole CTA.
 #include <mutex>
 
 #include "mcc_kernels.h"
@@ -24,7 +24,7 @@ constexpr int kScanThreads = 1024;
 constexpr int kSegCap = 12288;  // indices sorted in shared memory per segment; larger segments sort in place
 constexpr int kSegCapW = 4096;  // weight-order keys sorted in shared memory per segment; larger ones in the workspace
 
-constexpr int kWarpSeg = 512;  // segments up to this size are sorted by one warp in registers
+constexpr int kWarpSeg = 512;  // segments up to this size are sorted by one warp
 
 // Key of particle i (cell * S + species), or -1 past the end or out of range (latched).
 __device__ __forceinline__ long long bin_key(const int32_t* __restrict__ cell, const int32_t* __restrict__ species,
@@ -100,60 +100,55 @@ __global__ void k_scatter(const int32_t* __restrict__ cell, const int32_t* __res
     }
 }
 
-// One warp per segment of 2 .. kWarpSeg entries: the segment's indices in registers (K per lane), bitonic sort.
-// Every lane loads before the network's first shuffle and stores after its last, so the sort may run in place.
-template <int K>
-__device__ __noinline__ void warp_sort_seg_i32(int32_t* p, int n)
+// Ascending sort of n <= kWarpSeg keys in the calling warp's shared-memory slice: the bitonic network in its
+// "flip" form (every comparator puts the minimum at the lower index, so positions >= n act as +infinity and are
+// skipped), one warp barrier per stage. Loops stay rolled: the code is small enough to stay in the instruction cache.
+template <class T>
+__device__ __forceinline__ void warp_sort_smem(T* a, int n)
 {
     const int lane = threadIdx.x & 31;
-    uint64_t x[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        x[r] = pos < n ? (uint64_t)(uint32_t)p[pos] : ~0ull;
-    }
-    warp_bitonic<K>(x);
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        if (pos < n) p[pos] = (int32_t)(uint32_t)x[r];
+    int logP = 0;
+    while ((1 << logP) < n) ++logP;
+    const int half_work = 1 << (logP - 1);
+#pragma unroll 1
+    for (int lg = 1; lg <= logP; ++lg) {
+        const int size = 1 << lg, hmask = (size >> 1) - 1;
+#pragma unroll 1
+        for (int i = lane; i < half_work; i += 32) {
+            const int lo = ((i >> (lg - 1)) << lg) + (i & hmask), hi = ((i >> (lg - 1)) << lg) + size - 1 - (i & hmask);
+            if (hi < n) {
+                const T x = a[lo], y = a[hi];
+                if (x > y) { a[lo] = y; a[hi] = x; }
+            }
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int ls = lg - 2; ls >= 0; --ls) {
+            const int stride = 1 << ls;
+#pragma unroll 1
+            for (int i = lane; i < half_work; i += 32) {
+                const int lo = ((i >> ls) << (ls + 1)) + (i & (stride - 1)), hi = lo + stride;
+                if (hi < n) {
+                    const T x = a[lo], y = a[hi];
+                    if (x > y) { a[lo] = y; a[hi] = x; }
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
-// The weight order of one segment of 2 .. kWarpSeg entries (already in index order) by one warp: keys
-// weight_key(w, rank) sorted in registers, then each slot takes the index its key's rank points to; all reads of
-// the segment finish (warp barrier) before the first write.
-template <int K>
-__device__ __noinline__ void warp_sort_seg_w(const double* __restrict__ w, int32_t* p, int n)
-{
-    const int lane = threadIdx.x & 31;
-    uint64_t x[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        x[r] = pos < n ? weight_key(w[p[pos]], (uint32_t)pos) : ~0ull;
-    }
-    warp_bitonic<K>(x);
-    int32_t v[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        const int src = (int)(x[r] & kPermMask);
-        v[r] = pos < n ? p[src < n ? src : pos] : 0;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        if (pos < n) p[pos] = v[r];
-    }
-}
-
-// Small segments, one warp each (the loop index is warp-uniform, so whole warps take the same branches).
+// Small segments (2 .. kWarpSeg entries), one warp each, sorted in the warp's shared-memory slice (the loop index is
+// warp-uniform, so whole warps take the same branches). w == nullptr: the entries by particle index. Otherwise the
+// segment is already in index order and is put in the weight order: keys weight_key(w, rank) sorted, then each slot
+// takes the index its key's rank points to (every read of the segment finishes before the first write).
 __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __restrict__ offsets, int64_t nk,
                                                               const double* __restrict__ w, int32_t* __restrict__ perm)
 {
+    __shared__ uint64_t slab[kBinThreads / 32][kWarpSeg];
+    const int lane = threadIdx.x & 31;
+    uint64_t* buf = slab[threadIdx.x >> 5];
+    int32_t* ibuf = reinterpret_cast<int32_t*>(buf);
     const int64_t warp = ((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kBinThreads) >> 5;
     for (int64_t seg = warp; seg < nk; seg += nwarps) {
@@ -162,18 +157,22 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __r
         if (n < 2 || n > kWarpSeg) continue;
         int32_t* p = perm + b;
         if (w == nullptr) {
-            if (n <= 32) warp_sort_seg_i32<1>(p, n);
-            else if (n <= 64) warp_sort_seg_i32<2>(p, n);
-            else if (n <= 128) warp_sort_seg_i32<4>(p, n);
-            else if (n <= 256) warp_sort_seg_i32<8>(p, n);
-            else warp_sort_seg_i32<16>(p, n);
+            for (int i = lane; i < n; i += 32) ibuf[i] = p[i];
+            __syncwarp();
+            warp_sort_smem(ibuf, n);
+            for (int i = lane; i < n; i += 32) p[i] = ibuf[i];
         } else {
-            if (n <= 32) warp_sort_seg_w<1>(w, p, n);
-            else if (n <= 64) warp_sort_seg_w<2>(w, p, n);
-            else if (n <= 128) warp_sort_seg_w<4>(w, p, n);
-            else if (n <= 256) warp_sort_seg_w<8>(w, p, n);
-            else warp_sort_seg_w<16>(w, p, n);
+            for (int i = lane; i < n; i += 32) buf[i] = weight_key(w[p[i]], (uint32_t)i);
+            __syncwarp();
+            warp_sort_smem(buf, n);
+            for (int i = lane; i < n; i += 32) {
+                const int src = (int)(buf[i] & kPermMask);
+                buf[i] = (uint64_t)(uint32_t)p[src < n ? src : i];
+            }
+            __syncwarp();
+            for (int i = lane; i < n; i += 32) p[i] = (int32_t)(uint32_t)buf[i];
         }
+        __syncwarp();
     }
 }
 
