@@ -20,8 +20,10 @@
  *   orc_push               pinned: exact dyadic displacements and wraps, cell ids against exact rational floors,
  *                          relativistic displacements against 50-digit decimal arithmetic.
  *   relativistic pieces    pinned by invariants (4-momentum conservation, Eq. alpha_Eq0 residual, gamma->1 limit);
- *                          the relativistic scatter kinematics have no printed formula and are otherwise
- *                          "parity unpinned" beyond those invariants.
+ *                          the relativistic scatter kinematics (no printed formula) against their definition by an
+ *                          independent route: 50-digit Lorentz boosts into the CM frame show an elastic rotation by
+ *                          exactly Theta, mirrored azimuths, and v_rel* as the CM velocity difference. The use of
+ *                          |p*|^2 v_rel* in s is a reading, pinned only by its classical limit.
  */
 #ifndef MCC_ORACLE_H
 #define MCC_ORACLE_H

@@ -416,3 +416,72 @@ def test_nxn_equal_weights_conserve_pairwise():
         assert np.abs(P1 - P0).max() < 1e-12 * np.abs(mw[k, None] * v0[k]).sum()
         assert abs(E1 - E0) < 1e-12 * E0
     assert np.abs(v1 - v0).max() > 1e-3
+
+
+def _boost_to_cm(mp, c, ma, mb, ui, uj):
+    """Lorentz boost (50-digit mpmath) into the pair's centre-of-momentum frame, built from 4-momenta: returns a
+    function mapping a lab 3-momentum of mass m to its CM 3-momentum."""
+    c = mp.mpf(c)
+    pa = [mp.mpf(ma) * mp.mpf(x) for x in ui]
+    pb = [mp.mpf(mb) * mp.mpf(x) for x in uj]
+    Ea = mp.sqrt((mp.mpf(ma) * c ** 2) ** 2 + sum(x * x for x in pa) * c ** 2)
+    Eb = mp.sqrt((mp.mpf(mb) * c ** 2) ** 2 + sum(x * x for x in pb) * c ** 2)
+    P = [x + y for x, y in zip(pa, pb)]
+    beta = [x * c / (Ea + Eb) for x in P]
+    b2 = sum(x * x for x in beta)
+    g = 1 / mp.sqrt(1 - b2)
+
+    def to_cm(p, m):
+        E = mp.sqrt((mp.mpf(m) * c ** 2) ** 2 + sum(x * x for x in p) * c ** 2)
+        bp = sum(b * x for b, x in zip(beta, p))
+        # p' = p + ((g - 1) (beta.p) / b^2 - g E / c) beta
+        k = (g - 1) * bp / b2 - g * E / c if b2 > 0 else 0
+        return [x + k * b for x, b in zip(p, beta)], E
+
+    return to_cm, pa, pb
+
+
+def test_relativistic_scatter_is_an_elastic_cm_rotation_by_theta():
+    """The relativistic scatter (a reading: the paper prints no kinematics) checked against its definition by an
+    independent route: 50-digit Lorentz boosts of the oracle's pre- and post-collision momenta into the pair's CM
+    frame. There the momenta stay opposite and keep their magnitude |p*| (elastic), turn by exactly Theta, the
+    azimuths phi and phi + pi mirror each other about p*, and v_rel* is the difference of the two CM velocities."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(17)
+    c = 1.0
+    for trial in range(40):
+        ma, mb = 1.0, float(rng.choice([1.0, 1836.0, 7.5]))
+        ui = rng.normal(size=3) * rng.choice([0.01, 1.0, 5.0])
+        uj = rng.normal(size=3) * rng.choice([0.1, 3.0])
+        th = rng.uniform(0.01, math.pi - 0.01)
+        ph = rng.uniform(0, 2 * math.pi)
+        st, omc = math.sin(th), 1 - math.cos(th)
+        to_cm, pa, pb = _boost_to_cm(mp, c, ma, mb, ui, uj)
+        sa, _ = to_cm(pa, ma)
+        sb, _ = to_cm(pb, mb)
+        assert max(abs(x + y) for x, y in zip(sa, sb)) < mp.mpf(1e-40) * (1 + mp.norm(sa))  # opposite in the CM
+        pstar = mp.norm(sa)
+        outs = []
+        for phi in (ph, ph + math.pi):
+            dp, pm, vrel = O.rel_scatter_dp(c, ma, mb, ui, uj, st, omc, phi)
+            pa2 = [x + mp.mpf(d) for x, d in zip(pa, dp)]
+            pb2 = [x - mp.mpf(d) for x, d in zip(pb, dp)]
+            sa2, _ = to_cm(pa2, ma)
+            sb2, _ = to_cm(pb2, mb)
+            tol = 1e-12 * float(pstar) + 1e-13 * float(mp.norm(pa) + mp.norm(pb))
+            assert float(mp.norm([x + y for x, y in zip(sa2, sb2)])) < tol
+            assert abs(float(mp.norm(sa2) - pstar)) < tol
+            cos_turn = sum(x * y for x, y in zip(sa, sa2)) / (pstar * mp.norm(sa2))
+            assert abs(float(cos_turn) - math.cos(th)) < 1e-10 * (1 + float(mp.norm(pa) + mp.norm(pb)) / float(pstar))
+            assert pm == pytest.approx(float(pstar), rel=1e-12)
+            # v_rel* = |v_a* - v_b*| with v* = p* c^2 / E*
+            Ea_cm = mp.sqrt((mp.mpf(ma) * c ** 2) ** 2 + pstar ** 2 * c ** 2)
+            Eb_cm = mp.sqrt((mp.mpf(mb) * c ** 2) ** 2 + mp.norm(sb) ** 2 * c ** 2)
+            va = [x * c ** 2 / Ea_cm for x in sa]
+            vb = [x * c ** 2 / Eb_cm for x in sb]
+            assert vrel == pytest.approx(float(mp.norm([x - y for x, y in zip(va, vb)])), rel=1e-12)
+            outs.append(sa2)
+        # phi and phi + pi: the scattered momenta mirror about p*, their sum is 2 cos(Theta) p*
+        mirror = [x + y - 2 * mp.cos(mp.mpf(th)) * z for x, y, z in zip(outs[0], outs[1], sa)]
+        assert float(mp.norm(mirror)) < 1e-10 * (float(pstar) + float(mp.norm(pa) + mp.norm(pb)))
