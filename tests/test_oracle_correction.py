@@ -242,7 +242,7 @@ EPS0 = 8.8541878128e-12
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
 
-def test1_equilibrium():
+def paper_test1_equilibrium():
     """Conservation of the T1 populations (n_A = 1e19/cc, U_A = 655 km/s, T = 500 eV; n_B = 1e20/cc at rest)."""
     g = GOLDEN["test1"]
     mi = g["A_mass_number"] * M_U - g["Z"] * M_E
@@ -254,7 +254,7 @@ def test1_equilibrium():
 
 
 def test_test1_closed_form():
-    Uf, Tf = test1_equilibrium()
+    Uf, Tf = paper_test1_equilibrium()
     assert Uf / 1e3 == pytest.approx(GOLDEN["test1"]["U_f_km_s"], abs=0.005)
     assert Tf / 1e3 == pytest.approx(GOLDEN["test1"]["T_f_keV"], abs=0.005)
 
@@ -296,7 +296,7 @@ def test_test1_relaxes_to_closed_form():
     p = O.Params(method=O.N97, dt=50e-15, dV=dV, eps0=EPS0, fE=0.05, seed=7)
     corr, fail = O.step(st, [q], [mi], 10.0, p, n_steps=4000)
     # equilibrium phase: time-average the population moments over 8 samples 500 steps apart
-    Uf, Tf = test1_equilibrium()
+    Uf, Tf = paper_test1_equilibrium()
     samples = []
     for k in range(8):
         p.step += 4000 if k == 0 else 500
