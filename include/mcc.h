@@ -173,8 +173,8 @@ int mcc_bin_weighted(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, 
  * mcc_bin_static: the same cell sort as mcc_bin for callers that cannot allocate device memory at all, such as
  * code running under an allocator that must not grow, inside a host callback or driver-level integration where
  * cudaMalloc is unavailable, or a caller without a context to own a workspace. It takes no context and no
- * workspace: its counters live in one file-scope device array of MCC_BIN_STATIC_MAX_KEYS segment counters (two
- * int32 arrays, about 16 MiB) that every GPU loading this library holds until the process exits. The paper has no
+ * workspace: its counters live in one file-scope device array of MCC_BIN_STATIC_MAX_KEYS segment counters (three
+ * int32 arrays, about 24 MiB) that every GPU loading this library holds until the process exits. The paper has no
  * counterpart; this is an allocation-free variant of mcc_bin.
  *   Arguments and outputs as mcc_bin; n_cells * n_species above MCC_BIN_STATIC_MAX_KEYS returns MCC_ERR_TOO_LARGE
  *   before any work is enqueued. It calls no cudaMalloc, cudaFree or allocating library routine.

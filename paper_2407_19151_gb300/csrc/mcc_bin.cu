@@ -11,10 +11,11 @@
 #include "mcc_kernels.h"
 
 // Counters of mcc_bin_static: every device that loads the library holds this array until the process exits.
-// counts | cursors, each 4 * kStaticBinKeys bytes rounded to 256 (the layout launch_bin expects).
+// counts | cursors | large-segment list, the layout launch_bin expects for kStaticBinKeys segments.
 constexpr int64_t kStaticBinKeys = 1 << 21;
 constexpr size_t kStaticBinHalf = ((size_t)kStaticBinKeys * sizeof(int32_t) + 255) & ~(size_t)255;
-static __device__ __align__(256) int32_t g_bin_static_scratch[2 * kStaticBinHalf / sizeof(int32_t)];
+constexpr size_t kStaticBinList = ((size_t)(kStaticBinKeys + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
+static __device__ __align__(256) int32_t g_bin_static_scratch[(2 * kStaticBinHalf + kStaticBinList) / sizeof(int32_t)];
 
 namespace mcc {
 namespace {
@@ -52,35 +53,88 @@ __global__ void k_hist(const int32_t* __restrict__ cell, const int32_t* __restri
     }
 }
 
-// Exclusive scan of nk counts into nk + 1 offsets by one CTA: per-thread contiguous chunks, a scan of the chunk
-// totals in shared memory, then each chunk writes its offsets.
-__global__ void __launch_bounds__(kScanThreads) k_scan(const int32_t* __restrict__ counts, int64_t nk,
-                                                       int64_t* __restrict__ offsets, int32_t* status)
+// Exclusive scan of nk counts into nk + 1 offsets, in three passes over tiles of kScanTile keys: each CTA scans its
+// tile (tile-local offsets) and leaves the tile's total in counts[first key of the tile]; one CTA scans the tile
+// totals in place (their exclusive prefixes) and writes offsets[nk]; each CTA adds its tile's prefix. The counts are
+// not read again after the scan, so their tile-start slots can carry the totals.
+constexpr int kScanTile = 4 * kScanThreads;
+
+// Exclusive scan of v over the CTA (kScanThreads threads); returns this thread's exclusive prefix, *total the sum.
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* wsum, int64_t* total)
 {
-    __shared__ int64_t part[kScanThreads];
-    const int64_t chunk = (nk + kScanThreads - 1) / kScanThreads;
-    const int64_t b = (int64_t)threadIdx.x * chunk;
-    const int64_t e = b + chunk < nk ? b + chunk : nk;
-    int64_t s = 0;
-    for (int64_t k = b; k < e; ++k) {
-        const int32_t x = counts[k];
-        if (x > (1 << kPermBits)) latch(status, kErrTooLarge);
-        s += x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    part[threadIdx.x] = s;
+    if (lane == 31) wsum[wid] = x;
     __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        const int64_t y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += y;
-        __syncthreads();
+    if (wid == 0) {
+        int64_t t = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;
     }
-    int64_t run = part[threadIdx.x] - s;
-    for (int64_t k = b; k < e; ++k) {
-        offsets[k] = run;
-        run += counts[k];
+    __syncthreads();
+    *total = wsum[31];
+    return x - v + (wid > 0 ? wsum[wid - 1] : 0);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(int32_t* __restrict__ counts, int64_t nk,
+                                                            int64_t* __restrict__ offsets, int32_t* status)
+{
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+    int32_t c[4];
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j] = base + j < nk ? counts[base + j] : 0;
+        if (c[j] > (1 << kPermBits)) latch(status, kErrTooLarge);
+        s += c[j];
     }
-    if (threadIdx.x == kScanThreads - 1) offsets[nk] = part[kScanThreads - 1];
+    int64_t total;
+    int64_t run = block_exclusive_scan(s, wsum, &total);  // every thread has read its counts before this returns
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < nk) offsets[base + j] = run;
+        run += c[j];
+    }
+    if (threadIdx.x == 0) counts[(int64_t)blockIdx.x * kScanTile] = (int32_t)total;  // total <= n <= INT32_MAX
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int32_t* __restrict__ counts, int64_t nk, int64_t tiles,
+                                                           int64_t* __restrict__ offsets)
+{
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int64_t chunk = (tiles + kScanThreads - 1) / kScanThreads;
+    const int64_t b = (int64_t)threadIdx.x * chunk;
+    const int64_t e = b + chunk < tiles ? b + chunk : tiles;
+    int64_t s = 0;
+    for (int64_t t = b; t < e; ++t) s += counts[t * kScanTile];
+    int64_t total;
+    int64_t run = block_exclusive_scan(s, wsum, &total);
+    for (int64_t t = b; t < e; ++t) {
+        const int32_t x = counts[t * kScanTile];
+        counts[t * kScanTile] = (int32_t)run;
+        run += x;
+    }
+    if (threadIdx.x == 0) offsets[nk] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(const int32_t* __restrict__ counts, int64_t nk,
+                                                           int64_t* __restrict__ offsets)
+{
+    if (blockIdx.x == 0) return;
+    const int64_t pre = counts[(int64_t)blockIdx.x * kScanTile];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads)
+        if (base + j < nk) offsets[base + j] += pre;
 }
 
 __global__ void k_scatter(const int32_t* __restrict__ cell, const int32_t* __restrict__ species, int64_t n,
@@ -139,11 +193,13 @@ __device__ __forceinline__ void warp_sort_smem(T* a, int n)
 }
 
 // Small segments (2 .. kWarpSeg entries), one warp each, sorted in the warp's shared-memory slice (the loop index is
-// warp-uniform, so whole warps take the same branches). w == nullptr: the entries by particle index. Otherwise the
+// warp-uniform, so whole warps take the same branches). With `large` given, the ids of the larger segments are
+// appended to it (large[0] the count, zeroed before), for the CTA-wide sorts. w == nullptr: the entries by particle index. Otherwise the
 // segment is already in index order and is put in the weight order: keys weight_key(w, rank) sorted, then each slot
 // takes the index its key's rank points to (every read of the segment finishes before the first write).
 __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __restrict__ offsets, int64_t nk,
-                                                              const double* __restrict__ w, int32_t* __restrict__ perm)
+                                                              const double* __restrict__ w, int32_t* __restrict__ perm,
+                                                              int32_t* __restrict__ large)
 {
     __shared__ uint64_t slab[kBinThreads / 32][kWarpSeg];
     const int lane = threadIdx.x & 31;
@@ -154,6 +210,7 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __r
     for (int64_t seg = warp; seg < nk; seg += nwarps) {
         const int64_t b = offsets[seg];
         const int n = (int)(offsets[seg + 1] - b);
+        if (n > kWarpSeg && large != nullptr && lane == 0) large[1 + atomicAdd(&large[0], 1)] = (int32_t)seg;
         if (n < 2 || n > kWarpSeg) continue;
         int32_t* p = perm + b;
         if (w == nullptr) {
@@ -176,14 +233,15 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __r
     }
 }
 
-__global__ void __launch_bounds__(kBinThreads) k_segsort(const int64_t* __restrict__ offsets, int64_t nk,
-                                                         int32_t* __restrict__ perm)
+__global__ void __launch_bounds__(kBinThreads) k_segsort(const int64_t* __restrict__ offsets,
+                                                         const int32_t* __restrict__ large, int32_t* __restrict__ perm)
 {
     __shared__ int32_t buf[kSegCap];
-    for (int64_t seg = blockIdx.x; seg < nk; seg += gridDim.x) {
+    const int32_t n_large = large[0];
+    for (int32_t q = blockIdx.x; q < n_large; q += gridDim.x) {
+        const int64_t seg = large[1 + q];
         const int64_t b = offsets[seg];
         const int n = (int)(offsets[seg + 1] - b);
-        if (n <= kWarpSeg) continue;  // sorted by k_segsort_warp
         if (n <= kSegCap) {
             for (int i = threadIdx.x; i < n; i += kBinThreads) buf[i] = perm[b + i];
             __syncthreads();
@@ -196,19 +254,21 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort(const int64_t* __restri
     }
 }
 
-// Weight order of every segment (run after k_segsort, so a segment's entries are in increasing particle index):
+// Weight order of every large segment (run after k_segsort, so a segment's entries are in increasing particle index):
 // keys = weight_key(w, rank) (descending weight truncated to 32 fraction bits, ties by rank = by index), sorted, then
 // each slot takes the index its key's rank points to. keys: [n] workspace, holds the keys of large segments and
 // the reordered indices before they are copied back.
-__global__ void __launch_bounds__(kBinThreads) k_segsort_w(const int64_t* __restrict__ offsets, int64_t nk,
+__global__ void __launch_bounds__(kBinThreads) k_segsort_w(const int64_t* __restrict__ offsets,
+                                                           const int32_t* __restrict__ large,
                                                            const double* __restrict__ w, int32_t* __restrict__ perm,
                                                            uint64_t* __restrict__ keys)
 {
     __shared__ uint64_t buf[kSegCapW];
-    for (int64_t seg = blockIdx.x; seg < nk; seg += gridDim.x) {
+    const int32_t n_large = large[0];
+    for (int32_t q = blockIdx.x; q < n_large; q += gridDim.x) {
+        const int64_t seg = large[1 + q];
         const int64_t b = offsets[seg];
         const int n = (int)(offsets[seg + 1] - b);
-        if (n <= kWarpSeg) continue;  // ordered by k_segsort_warp
         uint64_t* k = n <= kSegCapW ? buf : keys + b;
         for (int i = threadIdx.x; i < n; i += kBinThreads) k[i] = weight_key(w[perm[b + i]], (uint32_t)i);
         __syncthreads();
@@ -241,11 +301,19 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
+// Workspace: counts | cursors (one int32 per segment each) | large-segment list (count, then segment ids).
 size_t bin_workspace_bytes(int64_t n, int64_t n_keys)
 {
     (void)n;
     const size_t one = ((size_t)n_keys * sizeof(int32_t) + 255) & ~(size_t)255;
-    return 2 * one;
+    const size_t lst = ((size_t)(n_keys + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
+    return 2 * one + lst;
+}
+
+static int32_t* large_list(void* ws, int64_t nk)
+{
+    const size_t one = ((size_t)nk * sizeof(int32_t) + 255) & ~(size_t)255;
+    return reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) + 2 * one);
 }
 
 cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
@@ -255,19 +323,23 @@ cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, i
     const size_t one = ((size_t)nk * sizeof(int32_t) + 255) & ~(size_t)255;
     int32_t* counts = reinterpret_cast<int32_t*>(ws);
     int32_t* cursor = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) + one);
-    cudaError_t e = cudaMemsetAsync(ws, 0, 2 * one, st);
+    int32_t* large = large_list(ws, nk);
+    cudaError_t e = cudaMemsetAsync(ws, 0, bin_workspace_bytes(n, nk), st);
     if (e != cudaSuccess) return e;
     const int g = grid_for(n, kBinThreads);
     if (n > 0) k_hist<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, counts, status);
-    k_scan<<<1, kScanThreads, 0, st>>>(counts, nk, offsets, status);
+    const int64_t tiles = (nk + kScanTile - 1) / kScanTile;
+    k_scan_tile<<<(unsigned)tiles, kScanThreads, 0, st>>>(counts, nk, offsets, status);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(counts, nk, tiles, offsets);
+    k_scan_add<<<(unsigned)tiles, kScanThreads, 0, st>>>(counts, nk, offsets);
+    *launches += 3;
     if (n > 0) {
         k_scatter<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, offsets, cursor, perm);
-        k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, nullptr, perm);
-        const int gs = grid_for(nk * kBinThreads, kBinThreads);
-        k_segsort<<<gs, kBinThreads, 0, st>>>(offsets, nk, perm);
+        k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, nullptr, perm, large);
+        k_segsort<<<grid_for(n / (kWarpSeg + 1) * kBinThreads, kBinThreads), kBinThreads, 0, st>>>(offsets, large,
+                                                                                                 perm);
         *launches += 4;
     }
-    *launches += 1;
     return cudaGetLastError();
 }
 
@@ -284,9 +356,10 @@ cudaError_t launch_bin_weighted(const int32_t* cell, const int32_t* species, con
     cudaError_t e = launch_bin(cell, species, n, n_cells, n_species, perm, offsets, ws, status, st, launches);
     if (e != cudaSuccess || n == 0) return e;
     uint64_t* keys = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + bin_workspace_bytes(n, nk));
-    k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm);
-    const int gs = grid_for(nk * kBinThreads, kBinThreads);
-    k_segsort_w<<<gs, kBinThreads, 0, st>>>(offsets, nk, w, perm, keys);
+    const int32_t* large = large_list(ws, nk);  // filled by launch_bin's index pass
+    k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm, nullptr);
+    k_segsort_w<<<grid_for(n / (kWarpSeg + 1) * kBinThreads, kBinThreads), kBinThreads, 0, st>>>(offsets, large, w,
+                                                                                               perm, keys);
     *launches += 2;
     return cudaGetLastError();
 }
