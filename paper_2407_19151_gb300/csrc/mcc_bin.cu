@@ -154,11 +154,12 @@ __global__ void k_scatter(const int32_t* __restrict__ cell, const int32_t* __res
     }
 }
 
-// Ascending sort of n <= kWarpSeg keys in the calling warp's shared-memory slice: the bitonic network in its
-// "flip" form (every comparator puts the minimum at the lower index, so positions >= n act as +infinity and are
-// skipped), one warp barrier per stage. Loops stay rolled: the code is small enough to stay in the instruction cache.
-template <class T>
-__device__ __forceinline__ void warp_sort_smem(T* a, int n)
+// Ascending sort of n <= kWarpSeg entries in the calling warp's shared-memory slice: the bitonic network in its
+// "flip" form (every comparator puts the smaller entry at the lower index, so positions >= n act as +infinity and
+// are skipped), one warp barrier per stage. Loops stay rolled: the code is small enough to stay in the instruction
+// cache. cmpx(lo, hi) orders the entries at two positions.
+template <class Cmpx>
+__device__ __forceinline__ void warp_sort_smem(int n, Cmpx cmpx)
 {
     const int lane = threadIdx.x & 31;
     int logP = 0;
@@ -169,11 +170,9 @@ __device__ __forceinline__ void warp_sort_smem(T* a, int n)
         const int size = 1 << lg, hmask = (size >> 1) - 1;
 #pragma unroll 1
         for (int i = lane; i < half_work; i += 32) {
-            const int lo = ((i >> (lg - 1)) << lg) + (i & hmask), hi = ((i >> (lg - 1)) << lg) + size - 1 - (i & hmask);
-            if (hi < n) {
-                const T x = a[lo], y = a[hi];
-                if (x > y) { a[lo] = y; a[hi] = x; }
-            }
+            const int base = (i >> (lg - 1)) << lg;
+            const int lo = base + (i & hmask), hi = base + size - 1 - (i & hmask);
+            if (hi < n) cmpx(lo, hi);
         }
         __syncwarp();
 #pragma unroll 1
@@ -182,10 +181,7 @@ __device__ __forceinline__ void warp_sort_smem(T* a, int n)
 #pragma unroll 1
             for (int i = lane; i < half_work; i += 32) {
                 const int lo = ((i >> ls) << (ls + 1)) + (i & (stride - 1)), hi = lo + stride;
-                if (hi < n) {
-                    const T x = a[lo], y = a[hi];
-                    if (x > y) { a[lo] = y; a[hi] = x; }
-                }
+                if (hi < n) cmpx(lo, hi);
             }
             __syncwarp();
         }
@@ -193,42 +189,56 @@ __device__ __forceinline__ void warp_sort_smem(T* a, int n)
 }
 
 // Small segments (2 .. kWarpSeg entries), one warp each, sorted in the warp's shared-memory slice (the loop index is
-// warp-uniform, so whole warps take the same branches). With `large` given, the ids of the larger segments are
-// appended to it (large[0] the count, zeroed before), for the CTA-wide sorts. w == nullptr: the entries by particle index. Otherwise the
-// segment is already in index order and is put in the weight order: keys weight_key(w, rank) sorted, then each slot
-// takes the index its key's rank points to (every read of the segment finishes before the first write).
+// warp-uniform, so whole warps take the same branches). w == nullptr: the entries by particle index. Otherwise
+// straight into the weight order of mcc_bin_weighted: pairs (weight key with a zero rank field, particle index)
+// sorted lexicographically, which is descending truncated weight with ties in increasing index. The ids of the
+// larger segments are appended to `large` (large[0] the count, zeroed before) for the CTA-wide sorts.
 __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __restrict__ offsets, int64_t nk,
                                                               const double* __restrict__ w, int32_t* __restrict__ perm,
                                                               int32_t* __restrict__ large)
 {
-    __shared__ uint64_t slab[kBinThreads / 32][kWarpSeg];
+    __shared__ uint64_t kslab[kBinThreads / 32][kWarpSeg];
+    __shared__ int32_t islab[kBinThreads / 32][kWarpSeg];
     const int lane = threadIdx.x & 31;
-    uint64_t* buf = slab[threadIdx.x >> 5];
-    int32_t* ibuf = reinterpret_cast<int32_t*>(buf);
+    uint64_t* kb = kslab[threadIdx.x >> 5];
+    int32_t* ib = islab[threadIdx.x >> 5];
     const int64_t warp = ((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kBinThreads) >> 5;
     for (int64_t seg = warp; seg < nk; seg += nwarps) {
         const int64_t b = offsets[seg];
         const int n = (int)(offsets[seg + 1] - b);
-        if (n > kWarpSeg && large != nullptr && lane == 0) large[1 + atomicAdd(&large[0], 1)] = (int32_t)seg;
+        if (n > kWarpSeg && lane == 0) large[1 + atomicAdd(&large[0], 1)] = (int32_t)seg;
         if (n < 2 || n > kWarpSeg) continue;
         int32_t* p = perm + b;
         if (w == nullptr) {
-            for (int i = lane; i < n; i += 32) ibuf[i] = p[i];
+            for (int i = lane; i < n; i += 32) ib[i] = p[i];
             __syncwarp();
-            warp_sort_smem(ibuf, n);
-            for (int i = lane; i < n; i += 32) p[i] = ibuf[i];
+            warp_sort_smem(n, [ib](int lo, int hi) {
+                const int32_t x = ib[lo], y = ib[hi];
+                if (x > y) {
+                    ib[lo] = y;
+                    ib[hi] = x;
+                }
+            });
         } else {
-            for (int i = lane; i < n; i += 32) buf[i] = weight_key(w[p[i]], (uint32_t)i);
-            __syncwarp();
-            warp_sort_smem(buf, n);
             for (int i = lane; i < n; i += 32) {
-                const int src = (int)(buf[i] & kPermMask);
-                buf[i] = (uint64_t)(uint32_t)p[src < n ? src : i];
+                const int32_t q = p[i];
+                ib[i] = q;
+                kb[i] = weight_key(w[q], 0u);
             }
             __syncwarp();
-            for (int i = lane; i < n; i += 32) p[i] = (int32_t)(uint32_t)buf[i];
+            warp_sort_smem(n, [kb, ib](int lo, int hi) {
+                const uint64_t x = kb[lo], y = kb[hi];
+                const int32_t a = ib[lo], c = ib[hi];
+                if (x > y || (x == y && a > c)) {
+                    kb[lo] = y;
+                    kb[hi] = x;
+                    ib[lo] = c;
+                    ib[hi] = a;
+                }
+            });
         }
+        for (int i = lane; i < n; i += 32) p[i] = ib[i];
         __syncwarp();
     }
 }
@@ -316,8 +326,11 @@ static int32_t* large_list(void* ws, int64_t nk)
     return reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) + 2 * one);
 }
 
-cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
-                       int32_t* perm, int64_t* offsets, void* ws, int32_t* status, cudaStream_t st, int64_t* launches)
+// hist -> scan -> scatter -> small segments by one warp each (index order, or with w the weight order directly)
+// -> large segments by index, one CTA each.
+static cudaError_t bin_core(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
+                            int32_t n_species, const double* w, int32_t* perm, int64_t* offsets, void* ws,
+                            int32_t* status, cudaStream_t st, int64_t* launches)
 {
     const int64_t nk = (int64_t)n_cells * n_species;
     const size_t one = ((size_t)nk * sizeof(int32_t) + 255) & ~(size_t)255;
@@ -335,12 +348,18 @@ cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, i
     *launches += 3;
     if (n > 0) {
         k_scatter<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, offsets, cursor, perm);
-        k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, nullptr, perm, large);
+        k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm, large);
         k_segsort<<<grid_for(n / (kWarpSeg + 1) * kBinThreads, kBinThreads), kBinThreads, 0, st>>>(offsets, large,
                                                                                                  perm);
         *launches += 4;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
+                       int32_t* perm, int64_t* offsets, void* ws, int32_t* status, cudaStream_t st, int64_t* launches)
+{
+    return bin_core(cell, species, n, n_cells, n_species, nullptr, perm, offsets, ws, status, st, launches);
 }
 
 size_t bin_weighted_workspace_bytes(int64_t n, int64_t n_keys)
@@ -353,14 +372,13 @@ cudaError_t launch_bin_weighted(const int32_t* cell, const int32_t* species, con
                                 int32_t* status, cudaStream_t st, int64_t* launches)
 {
     const int64_t nk = (int64_t)n_cells * n_species;
-    cudaError_t e = launch_bin(cell, species, n, n_cells, n_species, perm, offsets, ws, status, st, launches);
+    cudaError_t e = bin_core(cell, species, n, n_cells, n_species, w, perm, offsets, ws, status, st, launches);
     if (e != cudaSuccess || n == 0) return e;
     uint64_t* keys = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + bin_workspace_bytes(n, nk));
-    const int32_t* large = large_list(ws, nk);  // filled by launch_bin's index pass
-    k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm, nullptr);
+    const int32_t* large = large_list(ws, nk);  // the segments above kWarpSeg, already in index order
     k_segsort_w<<<grid_for(n / (kWarpSeg + 1) * kBinThreads, kBinThreads), kBinThreads, 0, st>>>(offsets, large, w,
                                                                                                perm, keys);
-    *launches += 2;
+    *launches += 1;
     return cudaGetLastError();
 }
 
