@@ -47,13 +47,6 @@ def velocity_error(got: np.ndarray, ref: np.ndarray, offsets: np.ndarray) -> np.
     return np.abs(got - ref).max(axis=1) / population_scale(ref, offsets)
 
 
-def cell_error(err: np.ndarray, offsets: np.ndarray, n_cells: int, S: int) -> np.ndarray:
-    cell_of = np.repeat(np.arange(n_cells), np.diff(offsets[::S]))
-    out = np.zeros(n_cells)
-    np.maximum.at(out, cell_of, err)
-    return out
-
-
 def cell_moments(v: np.ndarray, w: np.ndarray, m, species: np.ndarray, offsets: np.ndarray, n_cells: int, S: int,
                  rel: bool = False, c: float = 1.0):
     """Per cell: momentum (3), kinetic energy, and the scales sum m w |v| and sum KE."""

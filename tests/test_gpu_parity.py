@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 from paper_2407_19151_gb300 import workloads as W
 
-from _parity import (F32_TOL, F64_TOL, cell_error, cell_moments, device_state, gpu_velocities, oracle_state,
+from _parity import (F32_TOL, F64_TOL, cell_moments, device_state, gpu_velocities, oracle_state,
                      velocity_error)
 
 pytestmark = pytest.mark.gpu

@@ -4,7 +4,6 @@ Philox-4x32-10 is checked against the published known-answer values of its autho
 (Random123); binning against numpy's stable sort; pairing against brute-force structure rules of the order-N
 method [Sec. 3.2, Fig. TApairing] and a chi-square test that every intra-species pairing is equally likely.
 """
-import itertools
 import math
 import os
 
