@@ -387,3 +387,24 @@ def test_invalid_arguments_rejected_on_host(mcc):
         with pytest.raises(mcc.MccError) as e:
             mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, _species(wl), wl.lnL, pp)
         assert e.value.code == -1
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_resume_from_saved_state_is_bit_exact(mcc, dtype):
+    """Checkpoint / resume: the state is (velocities, weights, step, seed) because every draw is keyed by the step, so
+    two steps, a copy of the state to the host and back, and two more steps give exactly four uninterrupted steps."""
+    import torch
+    wl = W.three_species(n_cells=50, mean_count=90, precision=dtype)
+    sp = _species(wl)
+    v, w, off = device_state(wl, dtype)
+    ref = [x.clone() for x in v]
+    pp, _ = _params(mcc, wl, step=20)
+    mcc.mcc_step_fused(*ref, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, pp, n_steps=4)
+    mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, pp, n_steps=2)
+    saved = [x.cpu().numpy().copy() for x in v]
+    restored = [torch.from_numpy(x).cuda() for x in saved]
+    pr, _ = _params(mcc, wl, step=22)
+    mcc.mcc_step_fused(*restored, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, pr, n_steps=2)
+    mcc.sync_status(0)
+    for a, b in zip(ref, restored):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())

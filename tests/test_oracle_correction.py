@@ -315,3 +315,18 @@ def test_test1_relaxes_to_closed_form():
     UB, TB, UA_, TA_ = np.mean(samples, axis=0)
     assert UB == pytest.approx(Uf, rel=0.03) and UA_ == pytest.approx(Uf, rel=0.1)
     assert TB == pytest.approx(Tf, rel=0.03) and TA_ == pytest.approx(Tf, rel=0.05)
+
+
+def test_oracle_resume_is_bit_exact():
+    """Checkpoint / resume on the oracle: four steps equal two steps, a saved copy of the state, then two more
+    steps from step + 2 (every draw is keyed by the step index)."""
+    wl = W.three_species(n_cells=12, mean_count=60, precision="f64")
+    p = O.Params(method=wl.method, dt=wl.dt * 3, seed=wl.seed, step=40)
+    a = O.State(wl.vx, wl.vy, wl.vz, wl.w, wl.offsets, wl.n_cells, wl.n_species)
+    O.step(a, wl.q, wl.m, wl.lnL, p, n_steps=4)
+    b = O.State(wl.vx, wl.vy, wl.vz, wl.w, wl.offsets, wl.n_cells, wl.n_species)
+    O.step(b, wl.q, wl.m, wl.lnL, p, n_steps=2)
+    saved = b.v().copy()
+    c = O.State(saved[:, 0], saved[:, 1], saved[:, 2], wl.w, wl.offsets, wl.n_cells, wl.n_species)
+    O.step(c, wl.q, wl.m, wl.lnL, O.Params(method=wl.method, dt=wl.dt * 3, seed=wl.seed, step=42), n_steps=2)
+    np.testing.assert_array_equal(a.v(), c.v())
