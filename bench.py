@@ -194,7 +194,7 @@ def cpu_baseline(wl, budget_s: float = 15.0, one_thread: bool = False):
 
 
 def run_reference(args):
-    rank, world, _ = dist_env()
+    rank, _, _ = dist_env()
     if rank != 0:
         return
     wl = make_workload(args.cells, 0, "f32", args.layout)
@@ -371,7 +371,6 @@ def adjoint_measure(dev):
     L = torch.tensor(wl.lnL, dtype=torch.float64, requires_grad=True)
     off = torch.from_numpy(wl.offsets).to(dev)
     sp_of = torch.from_numpy(wl.species_of_particles()).to(dev).long()
-    m = torch.tensor(wl.m, dtype=torch.float64, device=dev)[sp_of]
     species = list(zip(wl.q.tolist(), wl.m.tolist()))
     params = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
 
@@ -453,9 +452,10 @@ def run_ours(args):
 
     # K steps captured in one CUDA graph (one memset + one persistent kernel per step)
     g = torch.cuda.CUDAGraph()
+    launches_before = ctx.launch_count()
     with torch.cuda.graph(g):
         step(args.warmup, args.steps)
-    launches_before = ctx.launch_count()
+    graph_launches = ctx.launch_count() - launches_before  # this library's kernels in the captured region
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -553,7 +553,7 @@ def run_ours(args):
                      "note": "latency- and issue-bound (block barriers per interaction), not HBM-bound"},
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": args.steps + 1,  # one persistent step kernel per captured step + the cell-order kernel
+        "gpu_launches": graph_launches,  # one persistent step kernel per captured step + the cell-order kernel
         "correction_failures": fails,
         "fp64_step": fp64,
         "adjoint": adj,

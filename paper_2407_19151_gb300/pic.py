@@ -72,7 +72,7 @@ class PicLoop:
         fail = torch.zeros(max(self.n_cells, 1), dtype=torch.int32, device=dev)
         for _ in range(int(n_steps)):
             self.push_and_rebin(stream)
-            x, y, z, vx, vy, vz, w, sp = self.arrays
+            vx, vy, vz, w = self.arrays[3:7]
             p = dataclasses.replace(self.params, step=self.params.step + self.t)
             B.mcc_step_fused(vx, vy, vz, w, self.offsets, self.n_cells, self.n_species, self.sp, self.lnL, p,
                              n_steps=1, max_cell=max_cell, interactions=self.inter, corr_pairs=corr,
