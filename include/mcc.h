@@ -99,7 +99,20 @@ typedef struct {
     uint64_t* step_device; /* mcc_step_fused only (null: use step): the step index lives in device memory; step t of
                               a call draws with *step_device + t, and the call adds n_steps to it on its stream after
                               the last step, so that a CUDA graph captured from one call serves every later step */
+    double* residual;      /* mcc_step_fused only, nullable: [2 * n_cells] device doubles receiving, per cell of the
+                              last step, the conservation of the state held on chip before it is stored (float-float
+                              on the mixed path): max_d |P_d - P0_d| / sum m w |v| and |E - E0| / E0, P0 and E0 the
+                              cell's momentum and kinetic energy when the step loaded it (Sec. 4: the correction
+                              conserves both exactly). Written for every cell of at most the largest group capacity
+                              (mcc_group_capacities); other cells are left as they are. */
+    void** launch_events;  /* mcc_step_fused only, nullable: 2 * (MCC_GROUP_CLASSES + 1) cudaEvent_t created by the
+                              caller; in the last step of the call, events [2k] and [2k + 1] are recorded on the
+                              stream just before and after the kernel of size class k (k = MCC_GROUP_CLASSES: the
+                              one-CTA kernel of the cells above every class), back to back for a class that is not
+                              launched, so that each class kernel can be timed with cudaEventElapsedTime */
 } mcc_params;
+
+#define MCC_GROUP_CLASSES 5
 
 /* Create / destroy a context on `device`. The context owns only a small device buffer (status word, work-queue
  * counter) allocated here, once. */
@@ -284,11 +297,14 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t
 
 /*
  * mcc_step_fused: n_steps whole collision steps (Algorithm 1 for every interaction in list order, each step with
- * index params->step + t) in one persistent kernel launch per step. Each CTA takes cells from a work queue (largest
- * cells first, ordered once per call by a small kernel), stages
- * the cell in shared memory (or in its workspace slab when the cell is larger than the on-chip tile), runs pairing,
- * scatter and correction for every interaction, and writes the cell back. The result equals the sequence
- * mcc_pair / mcc_scatter / mcc_correct over the interactions.
+ * index params->step + t). A small kernel orders the cells once per call by size class (mcc_group_capacities),
+ * largest first; each step then launches one persistent kernel per non-empty class, in which a group of 32 << k
+ * threads takes cells from the class's work queue, stages the cell in shared memory, runs pairing, scatter and
+ * correction for every interaction and writes the cell back. Cells above every class run on a one-CTA kernel (from
+ * its workspace slab when larger than its on-chip tile). For MCC_F64 the result equals the sequence
+ * mcc_pair / mcc_scatter / mcc_correct over the interactions (up to rounding). For MCC_F32_MIXED the velocities of
+ * a cell are held as float-float on chip for the whole step, the pair kinematics run in float and every sum,
+ * coefficient and energy pair in float-float; they are rounded to float once, when stored.
  *   interactions   host int32 [2 * n_inter], pairs (a, b) with a <= b; interaction k uses index k in the counters
  *   max_cell       an upper bound on particles per cell (cells above it latch MCC_ERR_BOUNDS and are skipped)
  *   corr_pairs     [n_cells] device int32 or NULL: accumulated energy pairs
@@ -300,16 +316,43 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* 
                    int32_t n_inter, const mcc_params* params, int32_t n_steps, int32_t max_cell,
                    int32_t* corr_pairs, int32_t* fail_count, void* ws, size_t ws_bytes, mcc_stream stream);
 
-/* Particles staged on chip per cell by mcc_step_fused (0 = automatic: the largest tile with which four CTAs share
- * an SM's shared memory, or the largest cell if smaller). Cells above it run from the workspace slabs. Used by the
- * autotuner. */
+/* Particles staged on chip per cell by the one-CTA kernel of mcc_step_fused, which takes the cells above the
+ * largest group class (0 = automatic: the largest tile with which six CTAs share an SM's shared memory, or the
+ * largest cell if smaller). Cells above it run from the workspace slabs. */
 int mcc_set_tile_cap(mcc_ctx* ctx, int32_t cap);
+
+/* Size classes of mcc_step_fused's group kernels: class k (k = 0..4) runs groups of 32 << k threads and takes the
+ * cells of at most caps[k] particles (the smallest such k); cells above caps[4] run on the one-CTA kernel.
+ * particles_per_warp sets caps[k] = particles_per_warp << k (each capped by what one CTA's shared memory holds, 44
+ * bytes per particle); 0 = automatic: the capacity with which sixteen warps share an SM's shared memory, and caps[4]
+ * as large as one CTA's shared memory allows. Used by the autotuner. */
+int mcc_set_group_capacity(mcc_ctx* ctx, int32_t particles_per_warp);
+
+/* The five class capacities mcc_step_fused uses for this precision and mode (caps_out: host int32[5]). */
+int mcc_group_capacities(mcc_ctx* ctx, int32_t prec, int32_t relativistic, int32_t* caps_out);
 
 /* Synchronise `stream`, read and clear the device status word; returns MCC_OK or the first latched error. */
 int mcc_sync_status(mcc_ctx* ctx, mcc_stream stream);
 
 /* Number of kernel launches enqueued through this context since creation (for launch accounting). */
 int64_t mcc_launch_count(mcc_ctx* ctx);
+
+/* Bounds-checked builds (compiled with -DMCC_DEBUG_BOUNDS; mcc_debug_bounds_build() returns 1 there, 0 otherwise):
+ * the group kernels of mcc_step_fused check every index into the on-chip tile and every computed global index
+ * against its bound; the first violation latches MCC_ERR_BOUNDS and is recorded, and the access uses index 0
+ * instead. mcc_debug_record synchronises `stream` and returns (source line, index, bound, count of violations) in
+ * out[0..3] (all zero if none), then clears the record. In other builds the record stays zero. */
+int mcc_debug_record(mcc_ctx* ctx, mcc_stream stream, int32_t* out);
+int mcc_debug_bounds_build(void);
+
+/* Phase-timing builds (compiled with -DMCC_PHASE_CLOCKS; mcc_phase_clocks_build() returns 1 there, 0 otherwise):
+ * the group kernels of mcc_step_fused add, per cell visit, the SM clock cycles of each phase, as thread 0 of the
+ * group sees them (barrier waits included), to per-class counters. mcc_phase_clocks synchronises `stream`, returns
+ * out[8 * k + q] for class k (0..4) and phase q (0 load and weight order, 1 permutations, 2 pair loop, 3 momentum
+ * sums and B, 4 shift and energy sums, 5 energy pairs, 6 write-back; q = 7: cell visits) and clears the counters.
+ * out: host uint64[40]. In other builds the counters stay zero. */
+int mcc_phase_clocks(mcc_ctx* ctx, mcc_stream stream, uint64_t* out);
+int mcc_phase_clocks_build(void);
 
 const char* mcc_status_string(int status);
 

@@ -45,7 +45,8 @@ class _Params(C.Structure):
                 ("eps0", C.c_double), ("c", C.c_double), ("fE", C.c_double), ("sort_by_weight", C.c_int32),
                 ("max_corr_passes", C.c_int32), ("fail_policy", C.c_int32), ("correct", C.c_int32),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("cell_base", C.c_uint32),
-                ("weighting", C.c_int32), ("pairing", C.c_int32), ("step_device", C.c_void_p)]
+                ("weighting", C.c_int32), ("pairing", C.c_int32), ("step_device", C.c_void_p),
+                ("residual", C.c_void_p), ("launch_events", C.c_void_p)]
 
 
 @dataclass
@@ -68,6 +69,10 @@ class Params:
     weighting: int = 0   # 0: the paper's s; 1: duplicity weighting (w_max / D_ij, N_max) for inter-species pairs
     pairing: int = 0     # 0: order-N pairs; 1: all N x N pairs (fused step only)
     step_device: object = None  # optional int64/uint64 device tensor of one element holding the step (fused step)
+    residual: object = None     # optional float64 device tensor (2 * n_cells): per-cell conservation of the on-chip
+                                # state before the store (fused step)
+    launch_events: object = None  # optional list of 12 torch.cuda.Event(enable_timing=True): begin / end of each
+                                  # size class's kernel in the last step (fused step)
 
     def _c(self) -> _Params:
         return _Params(int(self.method), int(bool(self.relativistic)), float(self.dt), float(self.dV),
@@ -75,10 +80,25 @@ class Params:
                        int(self.max_corr_passes), int(self.fail_policy), int(bool(self.correct)),
                        int(self.seed) & (2**64 - 1), int(self.step) & (2**64 - 1), int(self.cell_base),
                        int(self.weighting), int(self.pairing),
-                       C.c_void_p(self.step_device.data_ptr()) if self.step_device is not None else C.c_void_p(0))
+                       C.c_void_p(self.step_device.data_ptr()) if self.step_device is not None else C.c_void_p(0),
+                       C.c_void_p(self.residual.data_ptr()) if self.residual is not None else C.c_void_p(0),
+                       _events(self.launch_events))
 
 
 _LIB = None
+_EVENT_ARRAYS = []
+
+
+def _events(events):
+    """Host array of the cudaEvent_t handles of a list of torch CUDA events (kept alive with the last call)."""
+    if events is None:
+        return C.c_void_p(0)
+    for e in events:
+        if e.cuda_event == 0:  # created lazily by torch: record once so that the handle exists
+            e.record()
+    arr = (C.c_void_p * len(events))(*[e.cuda_event for e in events])
+    _EVENT_ARRAYS[:] = [arr]
+    return C.cast(arr, C.c_void_p)
 
 
 def lib():
@@ -118,8 +138,14 @@ def lib():
                                      P(C.c_int32), C.c_int32, P(_Params), C.c_int32, C.c_int32, vp, vp, vp,
                                      C.c_size_t, vp]),
         "mcc_set_tile_cap": (C.c_int, [vp, C.c_int32]),
+        "mcc_set_group_capacity": (C.c_int, [vp, C.c_int32]),
+        "mcc_group_capacities": (C.c_int, [vp, C.c_int32, C.c_int32, P(C.c_int32)]),
         "mcc_sync_status": (C.c_int, [vp, vp]),
         "mcc_launch_count": (C.c_int64, [vp]),
+        "mcc_debug_record": (C.c_int, [vp, vp, P(C.c_int32)]),
+        "mcc_debug_bounds_build": (C.c_int, []),
+        "mcc_phase_clocks": (C.c_int, [vp, vp, P(C.c_uint64)]),
+        "mcc_phase_clocks_build": (C.c_int, []),
         "mcc_status_string": (C.c_char_p, [C.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -166,6 +192,28 @@ class Context:
 
     def set_tile_cap(self, cap: int):
         _check(lib().mcc_set_tile_cap(self.handle, int(cap)), "mcc_set_tile_cap")
+
+    def set_group_capacity(self, particles_per_warp: int):
+        _check(lib().mcc_set_group_capacity(self.handle, int(particles_per_warp)), "mcc_set_group_capacity")
+
+    def group_capacities(self, prec: int = F32_MIXED, relativistic: bool = False) -> list[int]:
+        caps = (C.c_int32 * 5)()
+        _check(lib().mcc_group_capacities(self.handle, int(prec), int(bool(relativistic)), caps),
+               "mcc_group_capacities")
+        return list(caps)
+
+    def debug_record(self, stream=None) -> list[int]:
+        """(source line, index, bound, count) of the first out-of-bounds index seen by a bounds-checked build."""
+        out = (C.c_int32 * 4)()
+        _check(lib().mcc_debug_record(self.handle, _stream(stream, self.device), out), "mcc_debug_record")
+        return list(out)
+
+    def phase_clocks(self, stream=None) -> list[list[int]]:
+        """Per group size class: cycles of the 7 phases of a cell visit and the number of visits (phase-timing
+        builds; zeros otherwise)."""
+        out = (C.c_uint64 * 40)()
+        _check(lib().mcc_phase_clocks(self.handle, _stream(stream, self.device), out), "mcc_phase_clocks")
+        return [list(out[8 * k: 8 * k + 8]) for k in range(5)]
 
     def sync_status(self, stream=None) -> int:
         return int(lib().mcc_sync_status(self.handle, _stream(stream, self.device)))

@@ -10,16 +10,18 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu", "mcc_adjoint.cu", "mcc_pic.cu"]
-HEADERS = ["mcc_device.cuh", "mcc_kernels.h", "mcc_pic.h"]
+SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu", "mcc_adjoint.cu", "mcc_pic.cu", "mcc_group_f32.cu",
+           "mcc_group_f32rel.cu"]
+HEADERS = ["mcc_device.cuh", "mcc_kernels.h", "mcc_pic.h", "mcc_group.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 EXTRA = os.environ.get("MCC_NVCC_FLAGS", "").split()
 
 
-def lib_path() -> str:
-    return os.path.join(BUILD, f"libmcc.{platform.machine()}.so")
+def lib_path(debug_bounds: bool = False, phase_clocks: bool = False) -> str:
+    tag = ("_bounds" if debug_bounds else "") + ("_clocks" if phase_clocks else "")
+    return os.path.join(BUILD, f"libmcc{tag}.{platform.machine()}.so")
 
 
 def _newest_input() -> float:
@@ -27,16 +29,20 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, out: str | None = None) -> str:
-    """Compile every translation unit in parallel, link the shared library; skip if up to date."""
-    out = out or lib_path()
+def build(force: bool = False, verbose: bool = False, out: str | None = None, debug_bounds: bool = False,
+          phase_clocks: bool = False) -> str:
+    """Compile every translation unit in parallel, link the shared library; skip if up to date. debug_bounds builds
+    the bounds-checked variant (-DMCC_DEBUG_BOUNDS), phase_clocks the phase-timing variant (-DMCC_PHASE_CLOCKS),
+    each into its own file."""
+    out = out or lib_path(debug_bounds, phase_clocks)
+    extra = EXTRA + (["-DMCC_DEBUG_BOUNDS"] if debug_bounds else []) + (["-DMCC_PHASE_CLOCKS"] if phase_clocks else [])
     if not force and os.path.exists(out) and os.path.getmtime(out) >= _newest_input():
         return out
     os.makedirs(os.path.dirname(out), exist_ok=True)
 
     def compile_one(src: str) -> str:
         obj = os.path.join(os.path.dirname(out), f"{os.path.splitext(src)[0]}.{os.path.basename(out)}.o")
-        cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -8,6 +8,8 @@
 #include "mcc_kernels.h"
 #include "mcc_pic.h"
 
+static_assert(mcc::kGroupClasses == MCC_GROUP_CLASSES, "size classes of the ABI and the kernels");
+
 struct mcc_ctx {
     int device;
     int32_t* dbuf;  // [0] status word, [1] work-queue counter, then the N97 tables
@@ -15,7 +17,9 @@ struct mcc_ctx {
     int num_sms;
     size_t smem_optin;
     size_t smem_per_sm;
-    int32_t tile_cap;  // particles staged on chip per cell; 0 = automatic
+    int32_t tile_cap;  // particles staged on chip per cell by the one-CTA kernel; 0 = automatic
+    int32_t group_cap; // particles per warp of the group kernels' size classes; 0 = automatic
+    size_t smem_reserved;  // shared memory the system reserves per CTA
 };
 
 namespace mcc {
@@ -88,7 +92,9 @@ using mcc::StepArgs;
 
 constexpr size_t kTabOffset = 64;  // bytes into the context buffer where the N97 tables start
 constexpr size_t kTabDoubles = 2 * (mcc::kN97Nodes + 1);
-constexpr size_t kCtxBytes = kTabOffset + kTabDoubles * sizeof(double) + kTabDoubles * sizeof(float);
+constexpr size_t kClkOffset = (kTabOffset + kTabDoubles * sizeof(double) + kTabDoubles * sizeof(float) + 63) & ~63;
+constexpr size_t kClkWords = 8 * mcc::kGroupClasses;  // phase cycles of the group kernels (phase-timing builds)
+constexpr size_t kCtxBytes = kClkOffset + kClkWords * sizeof(unsigned long long);
 
 constexpr size_t kStaticSmemReserve = 1024;  // margin above the cell kernel's static shared memory
 #ifndef MCC_AUTO_CTAS
@@ -187,6 +193,14 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
         a.fE = p->fE;
         a.c_f = (float)p->c;
         a.fE_f = (float)p->fE;
+        auto split = [](double x, float& hi, float& lo) {
+            hi = (float)x;
+            lo = (float)(x - (double)hi);
+        };
+        split(p->fE, a.fE_f, a.fE_lo);
+        split(-p->fE / (1.0 + std::sqrt(1.0 - p->fE)), a.gm1p_f, a.gm1p_lo);
+        split(p->fE / (1.0 + std::sqrt(1.0 + p->fE)), a.gm1n_f, a.gm1n_lo);
+        split(p->c > 0 ? 1.0 / (p->c * p->c) : 0.0, a.c2inv_f, a.c2inv_lo);
         a.rng.k0 = (uint32_t)p->seed;
         a.rng.k1 = (uint32_t)(p->seed >> 32);
         a.rng.step = (uint32_t)p->step;
@@ -201,6 +215,7 @@ int fill_args(StepArgs& a, const mcc_ctx* ctx, const mcc_particles* P, const int
     a.n97_dh = a.n97_f + (mcc::kN97Nodes + 1);
     a.n97_f32 = reinterpret_cast<const float*>(base + kTabDoubles * sizeof(double));
     a.n97_dh32 = a.n97_f32 + (mcc::kN97Nodes + 1);
+    a.phase_clk = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->dbuf) + kClkOffset);
     return MCC_OK;
 }
 
@@ -264,7 +279,10 @@ int mcc_create(mcc_ctx** out, int device)
     c->device = device;
     c->launches = 0;
     c->tile_cap = 0;
-    int optin = 0, sms = 0, per_sm = 0;
+    c->group_cap = 0;
+    int optin = 0, sms = 0, per_sm = 0, reserved = 0;
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    c->smem_reserved = (size_t)reserved;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
     c->smem_per_sm = (size_t)per_sm;
@@ -275,8 +293,13 @@ int mcc_create(mcc_ctx** out, int device)
     double tab[kTabDoubles];
     float tab32[kTabDoubles];
     mcc::n97_table(tab, tab + (mcc::kN97Nodes + 1));
-    for (size_t k = 0; k < kTabDoubles; ++k) tab32[k] = (float)tab[k];
-    if (cudaMalloc(&c->dbuf, kCtxBytes) != cudaSuccess || cudaMemset(c->dbuf, 0, kTabOffset) != cudaSuccess ||
+    // float copy: g = A s = exp(f) and h dg/dx = exp(f) (h df/dx)
+    for (int k = 0; k <= mcc::kN97Nodes; ++k) {
+        const double g = std::exp(tab[k]);
+        tab32[k] = (float)g;
+        tab32[mcc::kN97Nodes + 1 + k] = (float)(g * tab[mcc::kN97Nodes + 1 + k]);
+    }
+    if (cudaMalloc(&c->dbuf, kCtxBytes) != cudaSuccess || cudaMemset(c->dbuf, 0, kCtxBytes) != cudaSuccess ||
         cudaMemcpy(reinterpret_cast<char*>(c->dbuf) + kTabOffset, tab, sizeof tab, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(reinterpret_cast<char*>(c->dbuf) + kTabOffset + sizeof tab, tab32, sizeof tab32,
@@ -459,9 +482,10 @@ int mcc_correct(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
 }
 
 namespace {
-// Workspace of mcc_step_fused: the cell order (n_cells int32, 256-aligned), then one slab per resident CTA for the
-// cells larger than the on-chip tile.
+// Workspace of mcc_step_fused: the cell order (n_cells int32), the class bounds and queue counters of the group
+// kernels, then, when some cell exceeds the largest group class, one slab per resident CTA of the one-CTA kernel.
 size_t order_bytes(int32_t n_cells) { return ((size_t)n_cells * sizeof(int32_t) + 255) & ~(size_t)255; }
+constexpr size_t kCtrlBytes = 256;  // class_off [2 (kGroupClasses + 1)] and queues [kGroupClasses + 1], int32
 
 int tile_of(const mcc_ctx* ctx, bool f32)
 {
@@ -474,6 +498,43 @@ size_t slab_stride_of(int32_t max_cell, bool f32)
 {
     return ((size_t)max_cell * mcc::tile_bytes_per_particle(f32) + 255) & ~(size_t)255;
 }
+
+size_t group_static_smem(bool f32, bool rel, int cls)
+{
+    if (!f32) return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, mcc::group_kernel(f32, rel, cls)) != cudaSuccess) return 8192;
+    return fa.sharedSizeBytes;
+}
+
+constexpr int kAutoGroupWarpsPerSm = 16;  // automatic capacity: this many warps share one SM's shared memory
+
+// Capacity (particles) of each group size class. Class k runs 32 << k threads and holds cells of up to
+// per_warp << k particles, so that the shared memory per thread is the same in every class; the largest class
+// takes up to what one CTA's shared memory holds, unless the capacity is set explicitly.
+void group_caps(const mcc_ctx* ctx, bool f32, bool rel, int32_t caps[mcc::kGroupClasses])
+{
+    if (!f32) {  // FP64: every cell on the one-CTA kernel
+        for (int k = 0; k < mcc::kGroupClasses; ++k) caps[k] = 0;
+        return;
+    }
+    size_t per_warp;
+    if (ctx->group_cap > 0) {
+        per_warp = (size_t)ctx->group_cap;
+    } else {
+        const size_t per_cta = ctx->smem_per_sm / kAutoGroupWarpsPerSm;
+        const size_t fixed = ctx->smem_reserved + group_static_smem(f32, rel, 0);
+        per_warp = per_cta > fixed ? (per_cta - fixed) / mcc::kGroupBytesPerParticle : 32;
+    }
+    for (int k = 0; k < mcc::kGroupClasses; ++k) {
+        const size_t st = group_static_smem(f32, rel, k);
+        const size_t maxp = ctx->smem_optin > st ? (ctx->smem_optin - st) / mcc::kGroupBytesPerParticle : 0;
+        size_t cap = per_warp << k;
+        if (cap > maxp || (k == mcc::kGroupClasses - 1 && ctx->group_cap == 0)) cap = maxp;
+        if (cap > 65535) cap = 65535;  // cell-local indices are 16-bit
+        caps[k] = (int32_t)cap;
+    }
+}
 }  // namespace
 
 int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t max_cell, size_t* bytes)
@@ -481,9 +542,32 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t
     if (!ctx || !bytes || max_cell < 0 || n_cells < 0 || (prec != MCC_F64 && prec != MCC_F32_MIXED))
         return MCC_ERR_INVALID_ARG;
     const bool f32 = prec == MCC_F32_MIXED;
-    size_t total = order_bytes(n_cells);
-    if (max_cell > tile_of(ctx, f32)) total += slab_stride_of(max_cell, f32) * (size_t)ctx->num_sms * kMaxCtasPerSm;
+    int32_t caps[mcc::kGroupClasses];
+    group_caps(ctx, f32, false, caps);
+    int32_t caps_rel[mcc::kGroupClasses];
+    group_caps(ctx, f32, true, caps_rel);
+    const int32_t top = caps[mcc::kGroupClasses - 1] < caps_rel[mcc::kGroupClasses - 1]
+                            ? caps[mcc::kGroupClasses - 1]
+                            : caps_rel[mcc::kGroupClasses - 1];
+    size_t total = order_bytes(n_cells) + kCtrlBytes;
+    if (max_cell > top && max_cell > tile_of(ctx, f32))
+        total += slab_stride_of(max_cell, f32) * (size_t)ctx->num_sms * kMaxCtasPerSm;
     *bytes = total;
+    return MCC_OK;
+}
+
+int mcc_set_group_capacity(mcc_ctx* ctx, int32_t particles_per_warp)
+{
+    if (!ctx || particles_per_warp < 0) return MCC_ERR_INVALID_ARG;
+    ctx->group_cap = particles_per_warp;
+    return MCC_OK;
+}
+
+int mcc_group_capacities(mcc_ctx* ctx, int32_t prec, int32_t relativistic, int32_t* caps_out)
+{
+    if (!ctx || !caps_out || (prec != MCC_F64 && prec != MCC_F32_MIXED)) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    group_caps(ctx, prec == MCC_F32_MIXED, relativistic != 0, caps_out);
     return MCC_OK;
 }
 
@@ -502,31 +586,82 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
     if (n_cells == 0 || n_steps == 0) return MCC_OK;
     a.corr_pairs = corr_pairs;
     a.fail_count = fail_count;
+    a.resid = p->residual;
+    a.max_cell = max_cell;
     const bool f32 = P->prec == MCC_F32_MIXED;
     const bool rel = p->relativistic != 0;
     size_t need = 0;
     mcc_step_workspace_size(ctx, P->prec, n_cells, max_cell, &need);
     if (!ws || ws_bytes < need) return MCC_ERR_WORKSPACE;
-    const int tile = tile_of(ctx, f32);
-    const int cap = max_cell <= tile ? (max_cell > 0 ? max_cell : 1) : tile;
-    int max_grid = 1 << 30;
+    int32_t caps[mcc::kGroupClasses];
+    group_caps(ctx, f32, rel, caps);
+    // the group kernels serve the mixed path; the FP64 path runs every cell on the one-CTA kernel
+    const bool fallback = !f32 || max_cell > caps[mcc::kGroupClasses - 1];
     int32_t* order = reinterpret_cast<int32_t*>(ws);
-    if (max_cell > tile) {
-        a.slab = reinterpret_cast<char*>(ws) + order_bytes(n_cells);
-        a.slab_stride = (int64_t)slab_stride_of(max_cell, f32);
-        a.slab_cap = max_cell;
-        max_grid = (int)((ws_bytes - order_bytes(n_cells)) / (size_t)a.slab_stride);
-    }
-    // largest cells first (the order is the same for every step of the call)
-    if (mcc::launch_cell_order(offsets, n_cells, n_species, order, S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
+    int32_t* class_off = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) + order_bytes(n_cells));
+    int32_t* queues = class_off + 2 * (mcc::kGroupClasses + 1);
+    // cells by size class, largest first (the order is the same for every step of the call)
+    if (mcc::launch_group_order(offsets, n_cells, n_species, caps, order, class_off, S(stream)) != cudaSuccess)
+        return MCC_ERR_CUDA;
     ctx->launches += 1;
     a.order = order;
+    a.class_off = class_off;
+    a.queues = queues;
     a.step_dev = p->step_device;
+    // the one-CTA kernel takes the cells above every class from the order's first range
+    const int tile = tile_of(ctx, f32);
+    int max_grid = 1 << 30;
+    StepArgs big = a;
+    if (fallback) {
+        big.order_range = class_off + 2 * mcc::kGroupClasses;
+        if (max_cell > tile) {
+            big.slab = reinterpret_cast<char*>(ws) + order_bytes(n_cells) + kCtrlBytes;
+            big.slab_stride = (int64_t)slab_stride_of(max_cell, f32);
+            big.slab_cap = max_cell;
+            max_grid = (int)((ws_bytes - order_bytes(n_cells) - kCtrlBytes) / (size_t)big.slab_stride);
+        }
+    }
     for (int32_t t = 0; t < n_steps; ++t) {
         a.rng.step = (uint32_t)(p->step + (uint64_t)t);
         a.step_add = (uint32_t)t;
-        rc = run_cells(ctx, a, f32, rel, mcc::kFused, cap, S(stream), max_grid);
-        if (rc != MCC_OK) return rc;
+        if (cudaMemsetAsync(queues, 0, sizeof(int32_t) * (mcc::kGroupClasses + 1), S(stream)) != cudaSuccess)
+            return MCC_ERR_CUDA;
+        cudaEvent_t* ev = (p->launch_events && t == n_steps - 1) ? reinterpret_cast<cudaEvent_t*>(p->launch_events)
+                                                                   : nullptr;
+        auto mark = [&](int k, int end) {
+            if (ev) cudaEventRecord(ev[2 * k + end], S(stream));
+        };
+        mark(mcc::kGroupClasses, 0);
+        if (fallback) {
+            big.rng.step = a.rng.step;
+            big.step_add = a.step_add;
+            const int cap = max_cell <= tile ? max_cell : tile;
+            rc = run_cells(ctx, big, f32, rel, mcc::kFused, cap, S(stream), max_grid);
+            if (rc != MCC_OK) return rc;
+        }
+        mark(mcc::kGroupClasses, 1);
+        for (int cls = mcc::kGroupClasses - 1; cls >= 0; --cls) {
+            mark(cls, 0);
+            if (!f32 || (cls > 0 && caps[cls - 1] >= max_cell)) {  // no cell can be in this class
+                mark(cls, 1);
+                continue;
+            }
+            const size_t smem = (size_t)caps[cls] * mcc::kGroupBytesPerParticle;
+            const void* fn = mcc::group_kernel(f32, rel, cls);
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return MCC_ERR_CUDA;
+            int bps = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 32 << cls, smem) != cudaSuccess || bps < 1)
+                return MCC_ERR_CUDA;
+            int grid = bps * ctx->num_sms;
+            if (grid > n_cells) grid = n_cells;
+            a.gcls = cls;
+            a.gcap = caps[cls];
+            const cudaError_t e = mcc::launch_group(f32, rel, cls, a, grid, smem, S(stream));
+            ctx->launches += 1;
+            if (e != cudaSuccess) return MCC_ERR_CUDA;
+            mark(cls, 1);
+        }
     }
     if (p->step_device) {
         if (mcc::launch_step_advance(p->step_device, (uint64_t)n_steps, S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
@@ -587,6 +722,45 @@ int mcc_sync_status(mcc_ctx* ctx, mcc_stream stream)
 }
 
 int64_t mcc_launch_count(mcc_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int mcc_debug_record(mcc_ctx* ctx, mcc_stream stream, int32_t* out)
+{
+    if (!ctx || !out) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
+    if (cudaMemcpy(out, ctx->dbuf + 4, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return MCC_ERR_CUDA;
+    if (cudaMemset(ctx->dbuf + 4, 0, 4 * sizeof(int32_t)) != cudaSuccess) return MCC_ERR_CUDA;
+    return MCC_OK;
+}
+
+int mcc_phase_clocks(mcc_ctx* ctx, mcc_stream stream, uint64_t* out)
+{
+    if (!ctx || !out) return MCC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return MCC_ERR_CUDA;
+    char* p = reinterpret_cast<char*>(ctx->dbuf) + kClkOffset;
+    if (cudaMemcpy(out, p, kClkWords * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess) return MCC_ERR_CUDA;
+    if (cudaMemset(p, 0, kClkWords * sizeof(uint64_t)) != cudaSuccess) return MCC_ERR_CUDA;
+    return MCC_OK;
+}
+
+int mcc_phase_clocks_build(void)
+{
+#ifdef MCC_PHASE_CLOCKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int mcc_debug_bounds_build(void)
+{
+#ifdef MCC_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 int mcc_set_tile_cap(mcc_ctx* ctx, int32_t cap)
 {

@@ -3,7 +3,8 @@
 // One CTA owns one cell at a time (persistent CTAs pull cells from an atomic work queue). The cell's particles are
 // staged in shared memory as a tile: velocities, their pre-interaction copy, weights, sort keys and the random
 // permutation. For every interaction (a, b) of the step it then runs Algorithm 1 of the paper:
-//   random permutation(s) (Philox keys, bitonic sort)  -> Takizuka-Abe pairs (Sec. 3.2, Fig. TApairing)
+//   random permutation(s) (Philox keys, counting sort on the top key bits, insertion sort within a bucket)
+//     -> Takizuka-Abe pairs (Sec. 3.2, Fig. TApairing)
 //   pair loop: weighted scattering length (Eq. sab_TA77), TA77 / N97 angle, rotation, rejection of the heavier
 //              particle with probability 1 - w_min/w_max (Sec. 3.2); inter-species pairs in rounds of N_min
 //              disjoint pairs, rounds in order
@@ -253,39 +254,6 @@ __device__ __forceinline__ void partition_coef(const StepArgs& A, const InterCon
     sh.Df[0] = fabsf(D0.hi) <= 0x1p-47f * Ea.hi ? 0.f : D0.hi;
     sh.Df[1] = fabsf(D1.hi) <= 0x1p-47f * (intra ? 0.f : Eb.hi) ? 0.f : D1.hi;
     sh.fail = fail;
-}
-
-constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp in registers
-
-// Ascending sort of n <= 512 keys in buf (shared or global) by the calling warp: loaded K per lane into registers,
-// bitonic network, stored back. One out-of-line copy per K keeps register pressure and code size off the callers.
-template <int K>
-__device__ __noinline__ void warp_sort_buf_k(uint64_t* buf, int n)
-{
-    const int lane = threadIdx.x & 31;
-    uint64_t x[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        x[r] = pos < n ? buf[pos] : ~0ull;
-    }
-    warp_bitonic<K>(x);
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        if (pos < n) buf[pos] = x[r];
-    }
-}
-
-__device__ __forceinline__ void warp_sort_buf(uint64_t* buf, int n)
-{
-    __syncwarp();
-    if (n <= 32) warp_sort_buf_k<1>(buf, n);
-    else if (n <= 64) warp_sort_buf_k<2>(buf, n);
-    else if (n <= 128) warp_sort_buf_k<4>(buf, n);
-    else if (n <= 256) warp_sort_buf_k<8>(buf, n);
-    else warp_sort_buf_k<16>(buf, n);
-    __syncwarp();
 }
 
 // Random permutations of the interaction's one or two species segments: local indices ordered by their 64-bit
@@ -606,15 +574,6 @@ __device__ __forceinline__ void scatter_pair(const StepArgs& A, const Tile<V>& t
 #pragma unroll
         for (int d = 0; d < 3; ++d) t.v[d * t.vs + j] = vj[d] + dvj[d];
     }
-}
-
-// Energy-correction pairs of fast particles (gamma > 2 for either) run in double on the mixed path: the pair's
-// CM kinetic energy and the Appendix-A quadratic lose ~gamma^2 of float precision for co-moving particles.
-template <class V>
-__device__ __forceinline__ bool fast_pair(V c, const V v1[3], const V v2[3])
-{
-    const V lim = (V)3 * c * c;  // |u|^2 > 3 c^2  <=>  gamma > 2
-    return (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]) > lim || (v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]) > lim;
 }
 
 // Energy-pair order of a species segment with partially tied weights: the interaction's random permutation, stably
@@ -1058,7 +1017,12 @@ __global__ void __launch_bounds__(kThreads, MCC_MIN_BLOCKS) cell_kernel(const __
     for (;;) {
         if (threadIdx.x == 0) {
             const int q = atomicAdd(A.queue, 1);
-            sh.cell = (q < A.n_cells && A.order) ? A.order[q] : q;
+            if (A.order_range) {
+                const int b = A.order_range[0], e = A.order_range[1];
+                sh.cell = b + q < e ? A.order[b + q] : A.n_cells;
+            } else {
+                sh.cell = (q < A.n_cells && A.order) ? A.order[q] : q;
+            }
         }
         __syncthreads();
         const int c = sh.cell;
@@ -1105,6 +1069,76 @@ __global__ void __launch_bounds__(kOrderThreads) k_cell_order(const int64_t* __r
         const int64_t n = offsets[(int64_t)(c + 1) * S] - offsets[(int64_t)c * S];
         const int cls = n > 0 ? 63 - __clzll((unsigned long long)n) : 0;
         order[atomicAdd(&hist[32 - (cls > 32 ? 32 : cls)], 1)] = c;
+    }
+}
+
+// Cells by group size class for the group kernels: class k holds cells of at most caps[k] particles (the smallest
+// such k), class kGroupClasses the cells above every class. The order lists the largest class first and, within a
+// class, cells by descending size in steps of an eighth of an octave (longest-processing-time order); class_off[2k]
+// and class_off[2k + 1] bound class k. One CTA; shared-memory counters.
+constexpr int kGroupSub = 256;
+constexpr int kGroupBins = (kGroupClasses + 1) * kGroupSub;
+
+__device__ __forceinline__ int group_bin(int64_t n, const int32_t* caps)
+{
+    int cls = kGroupClasses;
+    for (int k = kGroupClasses - 1; k >= 0; --k)
+        if (n <= caps[k]) cls = k;
+    const uint64_t x = n > 0 ? (uint64_t)n : 1ull;
+    const int lg = 63 - __clzll((unsigned long long)x);
+    const int frac = lg >= 3 ? (int)((x >> (lg - 3)) & 7ull) : (int)((x << (3 - lg)) & 7ull);
+    int sub = lg * 8 + frac;
+    sub = sub > kGroupSub - 1 ? kGroupSub - 1 : sub;
+    return (kGroupClasses - cls) * kGroupSub + (kGroupSub - 1 - sub);
+}
+
+struct GroupCaps {
+    int32_t cap[kGroupClasses];
+};
+
+__global__ void __launch_bounds__(kOrderThreads) k_group_order(const int64_t* __restrict__ offsets, int32_t n_cells,
+                                                              int32_t S, GroupCaps caps, int32_t* __restrict__ order,
+                                                              int32_t* __restrict__ class_off)
+{
+    __shared__ int hist[kGroupBins];
+    __shared__ int warp_tot[kOrderThreads / 32];
+    for (int b = threadIdx.x; b < kGroupBins; b += kOrderThreads) hist[b] = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_cells; c += kOrderThreads)
+        atomicAdd(&hist[group_bin(offsets[(int64_t)(c + 1) * S] - offsets[(int64_t)c * S], caps.cap)], 1);
+    __syncthreads();
+    // exclusive scan of the bins: each thread owns a run of consecutive bins
+    constexpr int kPer = (kGroupBins + kOrderThreads - 1) / kOrderThreads;
+    const int lo = threadIdx.x * kPer;
+    int local = 0;
+    for (int b = lo; b < lo + kPer && b < kGroupBins; ++b) local += hist[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    int run = inc - local;
+    for (int w = 0; w < warp; ++w) run += warp_tot[w];
+    __syncthreads();
+    for (int b = lo; b < lo + kPer && b < kGroupBins; ++b) {
+        const int x = hist[b];
+        hist[b] = run;
+        run += x;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kGroupClasses) {
+        const int cls = threadIdx.x;
+        const int b0 = (kGroupClasses - cls) * kGroupSub;
+        class_off[2 * cls] = hist[b0];
+        class_off[2 * cls + 1] = b0 + kGroupSub < kGroupBins ? hist[b0 + kGroupSub] : n_cells;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_cells; c += kOrderThreads) {
+        const int b = group_bin(offsets[(int64_t)(c + 1) * S] - offsets[(int64_t)c * S], caps.cap);
+        order[atomicAdd(&hist[b], 1)] = c;
     }
 }
 
@@ -1166,6 +1200,30 @@ cudaError_t launch_cell_order(const int64_t* offsets, int32_t n_cells, int32_t S
 {
     k_cell_order<<<1, kOrderThreads, 0, st>>>(offsets, n_cells, S, order);
     return cudaGetLastError();
+}
+
+cudaError_t launch_group_order(const int64_t* offsets, int32_t n_cells, int32_t S, const int32_t* caps,
+                               int32_t* order, int32_t* class_off, cudaStream_t st)
+{
+    GroupCaps gc;
+    for (int k = 0; k < kGroupClasses; ++k) gc.cap[k] = caps[k];
+    k_group_order<<<1, kOrderThreads, 0, st>>>(offsets, n_cells, S, gc, order, class_off);
+    return cudaGetLastError();
+}
+
+const void* group_kernel_f32(int cls);
+const void* group_kernel_f32rel(int cls);
+
+const void* group_kernel(bool f32, bool rel, int cls)
+{
+    if (!f32) return nullptr;  // the FP64 path runs on the one-CTA kernel
+    return rel ? group_kernel_f32rel(cls) : group_kernel_f32(cls);
+}
+
+cudaError_t launch_group(bool f32, bool rel, int cls, const StepArgs& a, int grid, size_t smem, cudaStream_t st)
+{
+    void* args[] = {const_cast<StepArgs*>(&a)};
+    return cudaLaunchKernel(group_kernel(f32, rel, cls), dim3(grid), dim3(32 << cls), args, smem, st);
 }
 
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st)

@@ -104,7 +104,7 @@ __device__ __forceinline__ uint64_t weight_key(double w, uint32_t rank)
 // Float-float ("double-single") accumulation for the mixed-precision path: error-free sum (Knuth) and product
 // (FMA) transformations, giving ~48-bit sums of float terms without the FP64 pipe.
 // ---------------------------------------------------------------------------------------------------------------
-struct ff {
+struct __align__(8) ff {
     float hi, lo;
 };
 
@@ -404,6 +404,69 @@ __device__ __forceinline__ void block_sort_i32(int32_t* a, int n)
     }
 }
 
+constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp in registers
+
+// Ascending sort of n <= 512 keys in buf (shared or global) by the calling warp: loaded K per lane into registers,
+// bitonic network, stored back. One out-of-line copy per K keeps register pressure and code size off the callers.
+template <int K>
+__device__ __noinline__ void warp_sort_buf_k(uint64_t* buf, int n)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t x[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        x[r] = pos < n ? buf[pos] : ~0ull;
+    }
+    warp_bitonic<K>(x);
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int pos = lane * K + r;
+        if (pos < n) buf[pos] = x[r];
+    }
+}
+
+__device__ __forceinline__ void warp_sort_buf(uint64_t* buf, int n)
+{
+    __syncwarp();
+    if (n <= 32) warp_sort_buf_k<1>(buf, n);
+    else if (n <= 64) warp_sort_buf_k<2>(buf, n);
+    else if (n <= 128) warp_sort_buf_k<4>(buf, n);
+    else if (n <= 256) warp_sort_buf_k<8>(buf, n);
+    else warp_sort_buf_k<16>(buf, n);
+    __syncwarp();
+}
+
+// Energy-correction pairs of fast particles (gamma > 2 for either) run in double on the mixed path: the pair's
+// CM kinetic energy and the Appendix-A quadratic lose ~gamma^2 of float precision for co-moving particles.
+template <class V>
+__device__ __forceinline__ bool fast_pair(V c, const V v1[3], const V v2[3])
+{
+    const V lim = (V)3 * c * c;  // |u|^2 > 3 c^2  <=>  gamma > 2
+    return (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]) > lim || (v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]) > lim;
+}
+
+// Centre-of-mass kinetic energy of a weighted relativistic pair (as pair_kecm) with the difference of the proper
+// velocities du given apart (formed from a more precise state by the caller).
+template <class V>
+__device__ __forceinline__ V pair_kecm_du(V c, V m1, V m2, const V v1[3], const V v2[3], const V du[3])
+{
+    const V c2 = c * c;
+    const V g1 = sqrt((V)1 + (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]) / c2);
+    const V g2 = sqrt((V)1 + (v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]) / c2);
+    V du2 = 0, ss = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        du2 += du[d] * du[d];
+        ss += du[d] * (v1[d] + v2[d]);
+    }
+    const V dg = ss / (c2 * (g1 + g2));
+    V grm1 = (V)0.5 * (du2 / c2 - dg * dg);
+    if (grm1 < (V)0) grm1 = 0;
+    const V Minv = sqrt((m1 + m2) * (m1 + m2) + (V)2 * m1 * m2 * grm1);
+    return (V)2 * m1 * m2 * c2 * grm1 / (Minv + m1 + m2);
+}
+
 // ---------------------------------------------------------------------------------------------------------------
 // N97: A(s) solves L(A) = coth A - 1/A = exp(-s), taken in the equivalent form G(A) = 1 - L(A) = -expm1(-s) so that
 // small s (large A) keeps full relative precision. G is decreasing and convex, so Newton converges from any start
@@ -453,7 +516,9 @@ __device__ __forceinline__ void n97_G_dG(float A, float& G, float& dG)
 }
 
 // Table of f(x) = ln(A s) over x = ln s in [kN97X0, kN97X0 + kN97Nodes * kN97H]: node k holds (f, h df/dx) for
-// cubic Hermite interpolation (error ~1e-9). Built on the host when a context is created.
+// cubic Hermite interpolation (error ~1e-9). Built on the host when a context is created. The float copy holds
+// g = A s = exp(f) and h dg/dx instead: |f| reaches 8.5, where a float entry of f would carry ~5e-7 of A's relative
+// error, while a float entry of g carries 6e-8.
 constexpr int kN97Nodes = 512;
 constexpr double kN97X0 = -6.907755278982137;  // ln 1e-3
 constexpr double kN97X1 = 2.4849066497880004;  // ln 12
@@ -461,8 +526,8 @@ constexpr double kN97H = (kN97X1 - kN97X0) / kN97Nodes;
 
 template <class V>
 struct N97Tab {
-    const V* f;   // kN97Nodes + 1 values of ln(A s)
-    const V* dh;  // kN97Nodes + 1 values of h d ln(A s) / d ln s
+    const V* f;   // kN97Nodes + 1 values of ln(A s) (double) or A s (float)
+    const V* dh;  // kN97Nodes + 1 values of h times their derivative in ln s
 };
 
 // First approximation of A(s): below s = 1e-3, A = 1/(1 - e^-s) (exact to rounding there, since G(A) = 1/A up to
@@ -484,6 +549,7 @@ __device__ __forceinline__ V n97_A_table(V s, V z, const N97Tab<V>& tab)
     const V t2 = t * t, t3 = t2 * t;
     const V f = ((V)2 * t3 - (V)3 * t2 + (V)1) * f0 + (t3 - (V)2 * t2 + t) * d0 + ((V)-2 * t3 + (V)3 * t2) * f1 +
                 (t3 - t2) * d1;
+    if (sizeof(V) == 4) return f / s;  // the float table holds A s
     return exp(f) / s;
 }
 

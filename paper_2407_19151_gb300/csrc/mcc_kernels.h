@@ -41,6 +41,10 @@ struct StepArgs {
     int32_t pairing;    // 0: order-N pairs; 1: all N x N pairs (fused step only)
     double c, fE;
     float c_f, fE_f;
+    float fE_lo;              // fE - fE_f: (fE_f, fE_lo) is fE as float-float
+    float gm1p_f, gm1p_lo;    // sqrt(1 - fE) - 1 as float-float (a capped energy pair that loses energy)
+    float gm1n_f, gm1n_lo;    // sqrt(1 + fE) - 1 as float-float (a capped energy pair that gains energy)
+    float c2inv_f, c2inv_lo;  // 1 / c^2 as float-float
     RngKey rng;
     const uint64_t* step_dev;  // step index in device memory (null: rng.step); step = *step_dev + step_add
     uint32_t step_add;
@@ -64,10 +68,24 @@ struct StepArgs {
     char* slab;         // per-CTA global slabs for larger cells (may be null)
     int64_t slab_stride;
     int32_t slab_cap;
+    const int32_t* order_range;  // one-CTA kernel: [begin, end) of `order` to take cells from (null: every cell)
+    // group kernels (mcc_group.cuh)
+    const int32_t* class_off;  // [2 * kGroupClasses + 2]: begin / end of each size class in `order` (last: the rest)
+    int32_t* queues;           // [kGroupClasses + 1] work-queue counters, one per class
+    int32_t gcls;              // size class of the launch
+    int32_t gcap;              // particles one group stages on chip in this class
+    int32_t max_cell;          // the caller's bound on particles per cell (larger cells latch kErrBounds)
+    double* resid;             // [2 * n_cells] or null: per-cell |dP| / sum m w |v| and |dE| / E of the exact state
+    unsigned long long* phase_clk;  // [8 * kGroupClasses] cycles per phase and class (phase-timing builds)
 };
+
+constexpr int kGroupClasses = 5;  // group sizes 32, 64, 128, 256, 512 threads
 
 // Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation, weight order).
 __host__ __device__ inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
+
+// Shared-memory bytes per particle of the group kernels' cell tile (state, weight, scratch, two orders).
+constexpr size_t kGroupBytesPerParticle = 44;
 
 // N97 table: (f, h df/dx) at kN97Nodes + 1 nodes, computed on the host in double.
 void n97_table(double* f, double* dh);
@@ -76,6 +94,13 @@ void n97_table(double* f, double* dh);
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_step_advance(uint64_t* step, uint64_t by, cudaStream_t st);
 cudaError_t launch_cell_order(const int64_t* offsets, int32_t n_cells, int32_t S, int32_t* order, cudaStream_t st);
+// Cells ordered by group size class (largest class first; class kGroupClasses = cells above every class), largest
+// first within a class; class_off receives each class's [begin, end) in `order`.
+cudaError_t launch_group_order(const int64_t* offsets, int32_t n_cells, int32_t S, const int32_t* caps,
+                               int32_t* order, int32_t* class_off, cudaStream_t st);
+// Group kernels (mcc_group_*.cu): class cls runs groups of 32 << cls threads.
+const void* group_kernel(bool f32, bool rel, int cls);
+cudaError_t launch_group(bool f32, bool rel, int cls, const StepArgs& a, int grid, size_t smem, cudaStream_t st);
 int cell_kernel_blocks_per_sm(bool f32, bool rel, int mode, size_t smem);
 cudaError_t set_cell_smem_limit(bool f32, bool rel, int mode, size_t smem);
 size_t cell_kernel_static_smem(bool f32, bool rel, int mode);

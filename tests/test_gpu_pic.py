@@ -147,9 +147,10 @@ def test_pic_loop_fp64(mcc, order):
 
 def test_pic_loop_relativistic_fp64(mcc):
     """Two relativistic push / re-bin / collision steps, FP64. Re-binning gathers, in some cells, a few co-moving
-    fast beam particles whose energy-correction pair is ill-conditioned: the oracle itself moves by ~2e-12 when its
-    inputs change by one ulp. Bound: 99.9% of particles within 1e-12, every particle within four times the oracle's
-    own one-ulp sensitivity (measured here) or 1e-12, whichever is larger."""
+    fast beam particles whose energy-correction pair is ill-conditioned: the oracle itself moves by ~2e-12 there when
+    its inputs change by one ulp, and any difference in rounding order moves it as much. Bound, per cell: every
+    particle within 1e-12, or four times the oracle's own one-ulp sensitivity in that cell (measured here), whichever
+    is larger; most cells keep 1e-12."""
     wl = W.relativistic_beam(n_cells=60, count_lo=16, count_hi=200, precision="f64")
     got, off, (pos, v, w, s, roff, vref), ok = _loop_pair(mcc, wl, "f64", 2)
     np.testing.assert_array_equal(off, roff)
@@ -158,15 +159,21 @@ def test_pic_loop_relativistic_fp64(mcc):
     v1 = [np.asarray(a, np.float64) * (1 + rng.choice([-1.0, 1.0], wl.n) * 2.0 ** -52) for a in (wl.vx, wl.vy, wl.vz)]
     *_, off1, vref1, _ = _oracle_loop(wl, "f64", 2, v0=v1)
     np.testing.assert_array_equal(off1, roff)
-    sens = velocity_error(vref1, vref, roff).max()
+    S = wl.n_species
+    cell_of = np.repeat(np.arange(wl.n_cells), np.diff(roff[::S]))
+    sens_p = velocity_error(vref1, vref, roff)
+    sens_c = np.zeros(wl.n_cells)
+    np.maximum.at(sens_c, cell_of, sens_p)
+    bound = np.maximum(F64_TOL, 4 * sens_c[cell_of])
     err = velocity_error(np.stack(got[3:6], axis=1), vref, roff)
-    assert np.quantile(err, 0.999) < F64_TOL, np.quantile(err, 0.999)
-    assert err.max() < max(F64_TOL, 4 * sens), (err.max(), sens)
+    worst = int(np.argmax(err / bound))
+    assert (err < bound).all(), (err[worst], sens_c[cell_of[worst]], int(cell_of[worst]))
+    assert (sens_c <= F64_TOL).mean() >= 0.8
 
 
 def test_pic_loop_mixed(mcc):
     """One push / re-bin / collision step on the mixed path: the push from identical float inputs gives identical
-    positions and binning; the collision step within the mixed whole-step bounds."""
+    positions and binning; the collision step within 2e-6 for every particle."""
     wl = W.three_species(n_cells=120, mean_count=120)
     got, off, (pos, v, w, s, roff, vref), ok = _loop_pair(mcc, wl, "f32", 1)
     np.testing.assert_array_equal(off, roff)
@@ -174,6 +181,5 @@ def test_pic_loop_mixed(mcc):
     for d in range(3):
         np.testing.assert_array_equal(got[d], pos[d])
     err = velocity_error(np.stack([a.astype(np.float64) for a in got[3:6]], axis=1), vref, roff)
-    assert ok.mean() >= 0.98
-    assert np.quantile(err[ok], 0.99) < F32_TOL
-    assert err[ok].max() < 2e-4
+    assert ok.all()
+    assert err.max() < F32_TOL, err.max()
