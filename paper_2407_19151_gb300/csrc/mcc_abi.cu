@@ -507,8 +507,6 @@ size_t group_static_smem(bool f32, bool rel, int cls)
     return fa.sharedSizeBytes;
 }
 
-constexpr int kAutoGroupWarpsPerSm = 16;  // automatic capacity: this many warps share one SM's shared memory
-
 // Capacity (particles) of each group size class. Class k runs 32 << k threads and holds cells of up to
 // per_warp << k particles, so that the shared memory per thread is the same in every class; the largest class
 // takes up to what one CTA's shared memory holds, unless the capacity is set explicitly.
@@ -522,8 +520,8 @@ void group_caps(const mcc_ctx* ctx, bool f32, bool rel, int32_t caps[mcc::kGroup
     if (ctx->group_cap > 0) {
         per_warp = (size_t)ctx->group_cap;
     } else {
-        const size_t per_cta = ctx->smem_per_sm / kAutoGroupWarpsPerSm;
-        const size_t fixed = ctx->smem_reserved + group_static_smem(f32, rel, 0);
+        const size_t per_cta = ctx->smem_per_sm / mcc::kGroupWarpsPerSm;
+        const size_t fixed = ctx->smem_reserved + group_static_smem(f32, rel, 0);  // per one-warp CTA
         per_warp = per_cta > fixed ? (per_cta - fixed) / mcc::kGroupBytesPerParticle : 32;
     }
     for (int k = 0; k < mcc::kGroupClasses; ++k) {

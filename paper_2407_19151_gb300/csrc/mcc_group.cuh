@@ -1434,11 +1434,6 @@ __device__ void gcell(const StepArgs& A, int c, unsigned char* dyn, GShared<G>& 
 #endif
 }
 
-#ifndef MCC_GROUP_WARPS_PER_SM
-#define MCC_GROUP_WARPS_PER_SM 16
-#endif
-constexpr int kGroupWarpsPerSm = MCC_GROUP_WARPS_PER_SM;  // register budget: this many warps resident per SM
-
 template <bool REL, int G>
 __global__ void __launch_bounds__(G, kGroupWarpsPerSm / (G / 32) > 0 ? kGroupWarpsPerSm / (G / 32) : 1)
     group_kernel(const __grid_constant__ StepArgs A)

@@ -80,6 +80,12 @@ struct StepArgs {
 };
 
 constexpr int kGroupClasses = 5;  // group sizes 32, 64, 128, 256, 512 threads
+#ifndef MCC_GROUP_WARPS_PER_SM
+#define MCC_GROUP_WARPS_PER_SM 16
+#endif
+// Warps of the group kernels resident per SM: their register budget (launch bounds) and the automatic capacity
+// (shared memory per warp) are both set for this many.
+constexpr int kGroupWarpsPerSm = MCC_GROUP_WARPS_PER_SM;
 
 // Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation, weight order).
 __host__ __device__ inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
