@@ -16,7 +16,6 @@ workload, and the oracle timed on the host cores on a bounded sample of cells.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import subprocess
@@ -42,8 +41,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=1 << 18, help="cells of the three-species workload")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--group-cap", type=int, default=None,
+                    help="group capacity, particles per warp (0: automatic); default: the autotuner's choice")
     ap.add_argument("--tile-cap", type=int, default=None,
-                    help="particles per cell staged in shared memory (0: automatic); default: the autotuner's choice")
+                    help="tile of the one-CTA kernel (0: automatic); default: the autotuner's choice")
     ap.add_argument("--layout", default="weight_ordered", choices=["weight_ordered", "generated"],
                     help="particle order within each (cell, species) segment: by descending weight, as mcc_bin_weighted "
                          "stores it, or as generated")
@@ -74,11 +75,8 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("mcc_cell.cu", "mcc_device.cuh", "mcc_kernels.h"):
-        with open(os.path.join(ROOT, "paper_2407_19151_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    from paper_2407_19151_gb300._build import source_hash
+    return source_hash()
 
 
 def ncu_entry(workload: str):
@@ -136,6 +134,8 @@ class ClockSampler:
     def summary(self):
         try:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            if not rows:
+                raise ValueError("no clock samples")
             sm = [float(r[0]) for r in rows]
             mx = [float(r[1]) for r in rows]
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -150,6 +150,21 @@ def make_workload(cells: int, rank: int, precision: str, layout: str = "weight_o
     from paper_2407_19151_gb300 import workloads as W
     wl = W.three_species(n_cells=cells, data_seed=1239 + 1000 * rank, precision=precision)
     return wl.weight_ordered() if layout == "weight_ordered" else wl
+
+
+PRECISION = ("f32 velocities and kinematics, f64 weights; float-float (about 2^-44) sums, coefficients and "
+             "on-chip cell state")
+
+
+def bench_config(wl, layout: str, world: int) -> dict:
+    """The workload description both arms print (same keys, same values)."""
+    return {"workload": "three_species", "n_cells": wl.n_cells, "n_particles": wl.n, "species": wl.n_species,
+            "interactions": len(wl.interactions()), "pairs_per_step": wl.pairs_per_step(), "method": "N97",
+            "max_cell": int(wl.counts.sum(axis=1).max()),
+            "layout": layout + (" (segments by descending weight, the mcc_bin_weighted order)"
+                                if layout == "weight_ordered" else ""),
+            "l2": f"no flush: {32 * wl.n / 1e9:.2g} GB of state read and written per step (129 MB L2)",
+            "parallelism": f"cells, {world} independent shard(s)"}
 
 
 def cpu_baseline(wl, budget_s: float = 15.0, one_thread: bool = False):
@@ -202,8 +217,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "three_species", "n_cells": wl.n_cells, "n_particles": wl.n,
-                       "layout": args.layout},
+            "config": bench_config(wl, args.layout, args.gpus),
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -408,6 +422,39 @@ def adjoint_measure(dev):
                            "lnL": float(L.grad.norm())}}
 
 
+CLASS_KERNELS = [f"group_kernel<false, {32 << k}>" for k in range(5)] + ["cell_kernel<float, 0, 0>"]
+
+
+def class_table(wl, caps, class_ms, hbm):
+    """Per size class (threads per cell 32 << k; last: the one-CTA kernel of the cells above every class): cells,
+    particles, mean launch time, and the HBM rate of its 32 algorithmic bytes per particle."""
+    n = wl.counts.sum(axis=1)
+    cls = np.searchsorted(np.asarray(caps), n, side="left")  # smallest class whose capacity holds the cell
+    rows = []
+    for k in range(len(caps) + 1):
+        sel = cls == k
+        parts = int(n[sel].sum())
+        ms = float(class_ms[k])
+        gbs = BYTES_PER_PARTICLE["f32"] * parts / (ms * 1e-3) / 1e9 if ms > 0 and parts else 0.0
+        rows.append({"kernel": CLASS_KERNELS[k], "capacity": int(caps[k]) if k < len(caps) else None,
+                     "cells": int(sel.sum()), "particles": parts, "ms": ms, "achieved_gbs": gbs,
+                     "frac": gbs / hbm})
+    return rows
+
+
+def issue_ceiling(entry, dom, clk_mhz: float, hbm: float):
+    """Instruction-issue ceiling of the dominant kernel: its warp instructions per particle (ncu, on the kernel
+    source recorded with them) at one warp instruction per cycle on each of the 4 schedulers of the 152 SMs."""
+    if not entry or entry.get("kernel") != dom["kernel"] or not entry.get("warp_instructions_per_particle_step"):
+        return None
+    ipp = float(entry["warp_instructions_per_particle_step"])
+    rate = 152 * 4 * clk_mhz * 1e6
+    floor_ms = ipp * dom["particles"] / rate * 1e3
+    return {"warp_instructions_per_particle": ipp, "issue_rate_per_s": rate, "floor_ms": floor_ms,
+            "frac": floor_ms / dom["ms"] if dom["ms"] > 0 else None,
+            "hbm_frac_at_floor": BYTES_PER_PARTICLE["f32"] * dom["particles"] / (floor_ms * 1e-3) / 1e9 / hbm, "sm_mhz": clk_mhz}
+
+
 def run_ours(args):
     import torch
 
@@ -440,21 +487,34 @@ def run_ours(args):
                            corr_pairs=corr, fail_count=fail)
 
     stream = torch.cuda.current_stream(dev)
-    if args.tile_cap is None:
-        tile = mcc.autotune_tile_cap(*v, w, off, C, S, species, wl.lnL, params, max_cell)
-    else:
-        tile = args.tile_cap
-        ctx.set_tile_cap(tile)
+    tuned = None
+    if args.group_cap is None or args.tile_cap is None:
+        tuned = mcc.autotune(*v, w, off, C, S, species, wl.lnL, params, max_cell)
+    if args.group_cap is not None:
+        ctx.set_group_capacity(args.group_cap)
+    if args.tile_cap is not None:
+        ctx.set_tile_cap(args.tile_cap)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(dev)
     mcc.sync_status(local)
 
-    # K steps captured in one CUDA graph (one memset + one persistent kernel per step)
+    # K steps captured in one CUDA graph, one mcc_step_fused call per step (cell order, queue reset, one kernel per
+    # size class); each call records begin / end events around every class kernel as graph nodes, so that each
+    # kernel's launches are timed on the stream they run on, inside the timed region
+    n_ev = 2 * (mcc.GROUP_CLASSES + 1)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    for ev in events:
+        for e in ev:
+            e.record(stream)
+    torch.cuda.synchronize(dev)
     g = torch.cuda.CUDAGraph()
     launches_before = ctx.launch_count()
     with torch.cuda.graph(g):
-        step(args.warmup, args.steps)
+        for k in range(args.steps):
+            params.launch_events = events[k]
+            step(args.warmup + k)
+    params.launch_events = None
     graph_launches = ctx.launch_count() - launches_before  # this library's kernels in the captured region
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -466,6 +526,8 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
+    class_ms = np.array([[ev[2 * c].elapsed_time(ev[2 * c + 1]) for c in range(mcc.GROUP_CLASSES + 1)]
+                         for ev in events]).mean(axis=0)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -475,10 +537,16 @@ def run_ours(args):
     ms_step = ms / args.steps
     value = pairs * world / (ms_step * 1e-3)
     hbm, peak_kind = peaks()
-    algo_bytes = BYTES_PER_PARTICLE["f32"] * N
-    achieved = algo_bytes / (ms_step * 1e-3) / 1e9
-    traffic = ncu_traffic("three_species")
     fails = int(fail.sum().item())
+    classes = class_table(wl, ctx.group_capacities(mcc.F32_MIXED, False), class_ms, hbm)
+    dom = max(classes, key=lambda r: r["ms"])
+    achieved = BYTES_PER_PARTICLE["f32"] * dom["particles"] / (dom["ms"] * 1e-3) / 1e9
+    entry = ncu_entry("three_species")
+    traffic = None
+    if entry and entry.get("kernel") == dom["kernel"] and entry.get("bytes_per_particle"):
+        traffic = entry["bytes_per_particle"] * dom["particles"]
+    clocks = clk.summary()
+    issue = issue_ceiling(entry, dom, clocks.get("sm_mhz") or 2070.0, hbm)
 
     # end to end through host buffers: each step copies its inputs in from pinned host memory and the updated
     # velocities back out, in cell chunks overlapped with the compute (host_pipeline.step_host); host wall time
@@ -538,20 +606,22 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "three_species", "n_cells": C, "n_particles": N, "species": S,
-                   "interactions": len(wl.interactions()), "pairs_per_step": pairs, "method": "N97",
-                   "precision": "f32 velocities and kinematics, f64 weights, float-float sums, f64 coefficients",
-                   "max_cell": max_cell, "graph_steps": args.steps, "tile_cap": tile or "auto",
-                   "layout": args.layout + (" (segments by descending weight, the mcc_bin_weighted order)"
-                                            if args.layout == "weight_ordered" else ""),
-                   "l2": "no flush: 4.3 GB state per step, far larger than the 129 MB L2",
-                   "parallelism": f"cells, {world} independent shard(s)"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes": f"{BYTES_PER_PARTICLE['f32']} B/particle x {N} particles per launch",
-                     "issue_slots_busy": (ncu_entry("three_species") or {}).get("issue_slots_busy"),
-                     "note": "latency- and issue-bound (block barriers per interaction), not HBM-bound"},
-        "clocks": clk.summary(),
+        "config": bench_config(wl, args.layout, world),
+        "launch": {"graph_steps": args.steps, "group_capacities": ctx.group_capacities(mcc.F32_MIXED, False),
+                   "group_cap": args.group_cap if args.group_cap is not None else tuned["group_cap"],
+                   "tile_cap": args.tile_cap if args.tile_cap is not None else tuned["tile_cap"],
+                   "autotune": tuned, "precision": PRECISION},
+        "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "launch_ms": dom["ms"],
+                     "algorithmic_bytes": f"{BYTES_PER_PARTICLE['f32']} B/particle x {dom['particles']} particles "
+                                          f"per launch (the cells of its size class)",
+                     "step": {"ms": ms_step, "achieved": BYTES_PER_PARTICLE["f32"] * N / (ms_step * 1e-3) / 1e9,
+                              "frac": BYTES_PER_PARTICLE["f32"] * N / (ms_step * 1e-3) / 1e9 / hbm},
+                     "classes": classes, "issue": issue,
+                     "note": "instruction-issue- and latency-bound (per-cell barriers, dependent float-float "
+                             "arithmetic), not HBM-bound"},
+        "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": graph_launches,  # one persistent step kernel per captured step + the cell-order kernel
         "correction_failures": fails,

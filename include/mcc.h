@@ -50,7 +50,10 @@ typedef enum { MCC_TA77 = 0, MCC_N97 = 1 } mcc_method;
 typedef enum { MCC_F64 = 0, MCC_F32_MIXED = 1 } mcc_precision;
 typedef enum { MCC_FAIL_ROLLBACK = 0, MCC_FAIL_MOMENTUM_ONLY = 1, MCC_FAIL_ERROR = 2 } mcc_fail_policy;
 
-/* Maximum species per call and maximum particles per (cell, species) segment. */
+/* Maximum species per call and maximum particles per (cell, species) segment. Cell-local particle indices are packed
+ * into 20 bits of the pairing keys; the entry points that take max_cell (mcc_step_fused, mcc_adjoint and their
+ * workspace sizes) return MCC_ERR_TOO_LARGE for max_cell above MCC_MAX_SEGMENT, and cells above max_cell latch
+ * MCC_ERR_BOUNDS and are skipped, so no segment above the limit is ever processed. */
 #define MCC_MAX_SPECIES 8
 #define MCC_MAX_SEGMENT (1 << 20)
 
@@ -109,7 +112,8 @@ typedef struct {
                               caller; in the last step of the call, events [2k] and [2k + 1] are recorded on the
                               stream just before and after the kernel of size class k (k = MCC_GROUP_CLASSES: the
                               one-CTA kernel of the cells above every class), back to back for a class that is not
-                              launched, so that each class kernel can be timed with cudaEventElapsedTime */
+                              launched, so that each class kernel can be timed with cudaEventElapsedTime; under
+                              stream capture they are recorded as event-record nodes of the graph */
 } mcc_params;
 
 #define MCC_GROUP_CLASSES 5
@@ -196,7 +200,11 @@ int mcc_bin_weighted(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, 
  *   Every call clears the counters it uses on its stream before use, but all calls share the one array: calls that
  *   overlap on the GPU (different streams, or a second call before the first finished) race.
  *   There is no status word: particles with out-of-range cell or species are dropped, which shows as
- *   offsets_out[last] < n.
+ *   offsets_out[last] < n, and a (cell, species) segment above MCC_MAX_SEGMENT particles is not reported here (the
+ *   context-owning mcc_bin latches MCC_ERR_TOO_LARGE for it). The step entry points catch it downstream: their
+ *   max_cell is at most MCC_MAX_SEGMENT, so such a cell latches MCC_ERR_BOUNDS and is skipped.
+ *   stream must belong to the current device (MCC_ERR_INVALID_ARG otherwise): the counters' address is the
+ *   current device's.
  */
 #define MCC_BIN_STATIC_MAX_KEYS (1 << 21)
 int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
@@ -306,7 +314,8 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t
  * a cell are held as float-float on chip for the whole step, the pair kinematics run in float and every sum,
  * coefficient and energy pair in float-float; they are rounded to float once, when stored.
  *   interactions   host int32 [2 * n_inter], pairs (a, b) with a <= b; interaction k uses index k in the counters
- *   max_cell       an upper bound on particles per cell (cells above it latch MCC_ERR_BOUNDS and are skipped)
+ *   max_cell       an upper bound on particles per cell, at most MCC_MAX_SEGMENT (else MCC_ERR_TOO_LARGE); cells
+ *                  above it latch MCC_ERR_BOUNDS and are skipped
  *   corr_pairs     [n_cells] device int32 or NULL: accumulated energy pairs
  *   fail_count     [n_cells] device int32 or NULL: accumulated failed corrections
  *   ws, ws_bytes   workspace of mcc_step_workspace_size bytes

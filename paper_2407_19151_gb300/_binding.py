@@ -71,8 +71,8 @@ class Params:
     step_device: object = None  # optional int64/uint64 device tensor of one element holding the step (fused step)
     residual: object = None     # optional float64 device tensor (2 * n_cells): per-cell conservation of the on-chip
                                 # state before the store (fused step)
-    launch_events: object = None  # optional list of 12 torch.cuda.Event(enable_timing=True): begin / end of each
-                                  # size class's kernel in the last step (fused step)
+    launch_events: object = None  # optional list of 2 (GROUP_CLASSES + 1) torch.cuda.Event(enable_timing=True):
+                                  # begin / end of each size class's kernel in the last step (fused step)
 
     def _c(self) -> _Params:
         return _Params(int(self.method), int(bool(self.relativistic)), float(self.dt), float(self.dV),
@@ -85,6 +85,7 @@ class Params:
                        _events(self.launch_events))
 
 
+GROUP_CLASSES = 5  # size classes of the group kernels (MCC_GROUP_CLASSES)
 _LIB = None
 _EVENT_ARRAYS = []
 
@@ -197,7 +198,7 @@ class Context:
         _check(lib().mcc_set_group_capacity(self.handle, int(particles_per_warp)), "mcc_set_group_capacity")
 
     def group_capacities(self, prec: int = F32_MIXED, relativistic: bool = False) -> list[int]:
-        caps = (C.c_int32 * 5)()
+        caps = (C.c_int32 * GROUP_CLASSES)()
         _check(lib().mcc_group_capacities(self.handle, int(prec), int(bool(relativistic)), caps),
                "mcc_group_capacities")
         return list(caps)
@@ -312,8 +313,9 @@ def mcc_bin_static(cell: torch.Tensor, species: torch.Tensor, n_cells: int, n_sp
         perm = torch.empty(n, dtype=torch.int32, device=cell.device)
     if offsets is None:
         offsets = torch.empty(n_cells * n_species + 1, dtype=torch.int64, device=cell.device)
-    _check(lib().mcc_bin_static(_ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
-                                _stream(stream, cell.device)), "mcc_bin_static")
+    with torch.cuda.device(cell.device):  # the library's counters are addressed on the current device
+        _check(lib().mcc_bin_static(_ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
+                                    _stream(stream, cell.device)), "mcc_bin_static")
     return perm, offsets
 
 

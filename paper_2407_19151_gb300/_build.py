@@ -24,6 +24,16 @@ def lib_path(debug_bounds: bool = False, phase_clocks: bool = False) -> str:
     return os.path.join(BUILD, f"libmcc{tag}.{platform.machine()}.so")
 
 
+def source_hash() -> str:
+    """Hash of every source the library is built from (keys the autotuner's cache and the profile records)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "mcc.h")]:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _newest_input() -> float:
     files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "mcc.h")]
     return max(os.path.getmtime(f) for f in files)

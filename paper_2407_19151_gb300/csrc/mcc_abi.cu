@@ -366,6 +366,12 @@ int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32
     if (n < 0 || n_cells <= 0 || n_species <= 0 || !offsets_out) return MCC_ERR_INVALID_ARG;
     if (n > 0 && (!cell || !species || !perm_out)) return MCC_ERR_INVALID_ARG;
     if (n > INT32_MAX || (int64_t)n_cells * n_species > mcc::static_bin_max_keys()) return MCC_ERR_TOO_LARGE;
+    if (stream) {  // the counters' address is the current device's: the stream must run there
+        int sdev = -1, cur = -1;
+        if (cudaStreamGetDevice(S(stream), &sdev) != cudaSuccess || cudaGetDevice(&cur) != cudaSuccess)
+            return MCC_ERR_CUDA;
+        if (sdev != cur) return MCC_ERR_INVALID_ARG;
+    }
     return cuda_status(mcc::launch_bin_static(cell, species, n, n_cells, n_species, perm_out, offsets_out,
                                               S(stream)));
 }
@@ -539,6 +545,7 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t
 {
     if (!ctx || !bytes || max_cell < 0 || n_cells < 0 || (prec != MCC_F64 && prec != MCC_F32_MIXED))
         return MCC_ERR_INVALID_ARG;
+    if (max_cell > MCC_MAX_SEGMENT) return MCC_ERR_TOO_LARGE;
     const bool f32 = prec == MCC_F32_MIXED;
     int32_t caps[mcc::kGroupClasses];
     group_caps(ctx, f32, false, caps);
@@ -577,6 +584,7 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
     if (!ctx || !P || !offsets || !sp || !lnL || !interactions || !valid_params(p) || n_steps < 0 || max_cell < 0)
         return MCC_ERR_INVALID_ARG;
     if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
+    if (max_cell > MCC_MAX_SEGMENT) return MCC_ERR_TOO_LARGE;  // in-cell indices are 20-bit key fields
     DeviceGuard g(ctx->device);
     StepArgs a;
     int rc = fill_args(a, ctx, P, offsets, n_cells, n_species, sp, lnL, interactions, n_inter, 0, p);
@@ -619,6 +627,13 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
             max_grid = (int)((ws_bytes - order_bytes(n_cells) - kCtrlBytes) / (size_t)big.slab_stride);
         }
     }
+    // under stream capture the marks become event-record nodes of the graph, so that a replay records them too
+    unsigned rec_flags = cudaEventRecordDefault;
+    if (p->launch_events) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(S(stream), &cs) != cudaSuccess) return MCC_ERR_CUDA;
+        if (cs == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+    }
     for (int32_t t = 0; t < n_steps; ++t) {
         a.rng.step = (uint32_t)(p->step + (uint64_t)t);
         a.step_add = (uint32_t)t;
@@ -627,7 +642,7 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
         cudaEvent_t* ev = (p->launch_events && t == n_steps - 1) ? reinterpret_cast<cudaEvent_t*>(p->launch_events)
                                                                    : nullptr;
         auto mark = [&](int k, int end) {
-            if (ev) cudaEventRecord(ev[2 * k + end], S(stream));
+            if (ev) cudaEventRecordWithFlags(ev[2 * k + end], S(stream), rec_flags);
         };
         mark(mcc::kGroupClasses, 0);
         if (fallback) {
@@ -672,6 +687,7 @@ int mcc_adjoint_workspace_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, 
                                size_t* bytes)
 {
     if (!ctx || !bytes || n_cells < 0 || max_cell < 0 || max_corr_passes < 0) return MCC_ERR_INVALID_ARG;
+    if (max_cell > MCC_MAX_SEGMENT) return MCC_ERR_TOO_LARGE;
     const int32_t mc = max_cell > 0 ? max_cell : 1;
     const int32_t ep = max_corr_passes * (mc / 2 + 1) + 1;
     const int grid = adjoint_grid(ctx, n_cells);
@@ -686,6 +702,7 @@ int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
 {
     if (!ctx || !P || !offsets || !sp || !lnL || !valid_params(p) || inter < 0 || inter > 0xFFFFFF || max_cell < 0)
         return MCC_ERR_INVALID_ARG;
+    if (max_cell > MCC_MAX_SEGMENT) return MCC_ERR_TOO_LARGE;
     if (P->prec != MCC_F64 || p->relativistic || p->weighting != 0 || p->pairing != 0) return MCC_ERR_INVALID_ARG;
     const bool fwd = vx_out || vy_out || vz_out, rev = gvx || gvy || gvz;
     if (fwd && !(vx_out && vy_out && vz_out)) return MCC_ERR_INVALID_ARG;

@@ -478,6 +478,19 @@ def test_oversize_cell_latches_bounds(mcc):
     assert e.value.code == -6
 
 
+def test_max_cell_above_segment_limit_rejected(mcc):
+    """In-cell particle indices are 20-bit key fields: max_cell above MCC_MAX_SEGMENT is refused on the host
+    (MCC_ERR_TOO_LARGE) before any work, so a segment past the limit (which mcc_bin_static does not report) can only
+    reach the step as a cell above max_cell, which latches MCC_ERR_BOUNDS."""
+    wl = W.equilibration(n_cells=4, mean_count=30, precision="f32")
+    v, w, off = device_state(wl, "f32")
+    pp, _ = _params(mcc, wl)
+    with pytest.raises(mcc.MccError) as e:
+        mcc.mcc_step_fused(*v, w, off, wl.n_cells, wl.n_species, _species(wl), wl.lnL, pp, max_cell=(1 << 20) + 1)
+    assert e.value.code == -7
+    mcc.sync_status(0)
+
+
 def test_invalid_arguments_rejected_on_host(mcc):
     wl = W.equilibration(n_cells=2, mean_count=4, precision="f64")
     v, w, off = device_state(wl, "f64")
