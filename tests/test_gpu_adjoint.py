@@ -1,10 +1,12 @@
 """GPU parity of the pathwise adjoint (mcc_adjoint, collision_steps) against the oracle: its recomputed forward
 against the oracle step, its gradients against the closed forms that exact momentum and energy conservation fix,
-and against central differences of the oracle step on the same seed."""
+against the reverse-mode oracle gradient (oracle/autodiff.py) entry by entry over every particle, and against
+central differences of the oracle step on the same seed."""
 import numpy as np
 import pytest
 
 import oracle as O
+from oracle import autodiff as AD
 from oracle import gradient as G
 from paper_2407_19151_gb300 import workloads as W
 
@@ -148,6 +150,25 @@ def test_adjoint_matches_oracle_finite_differences(mcc, method, case):
             assert abs(gL[a, b] - g) <= tol, (a, b, gL[a, b], g)
             checked += 1
     assert checked >= 25
+
+
+@pytest.mark.parametrize("case", ["even", "poisson"])
+@pytest.mark.parametrize("method", [W.TA77, W.N97])
+def test_adjoint_equals_oracle_autodiff(mcc, method, case):
+    """A random cotangent over two steps: every entry of dL/dv, dL/dw and dL/dlnL of the CUDA adjoint against the
+    reverse-mode oracle gradient (torch autograd through the step transcribed on the CPU, decisions held fixed).
+    Tolerance 1e-9 of each gradient's largest entry (FP64 on both sides, different summation orders)."""
+    wl, kw = _case(method, n_cells=8, per_species=24) if case == "even" else _poisson_case(method)
+    rng = np.random.default_rng(17)
+    cot = rng.standard_normal((wl.n, 3))
+    vf, gv, gw, gL = _grads(mcc, wl, kw, lambda vf: cot)
+    v0 = np.stack([wl.vx, wl.vy, wl.vz], axis=1)
+    vo, gvo, gwo, gLo = AD.gradient(cot, v0, wl.w, wl.lnL, wl.offsets, wl.n_cells, wl.n_species, wl.q, wl.m,
+                                    O.Params(**kw), 2)
+    assert np.abs(vf - vo).max() <= 1e-12 * np.abs(vo).max()
+    assert np.abs(gv - gvo).max() <= 1e-9 * np.abs(gvo).max(), np.unravel_index(np.argmax(np.abs(gv - gvo)), gv.shape)
+    assert np.abs(gw - gwo).max() <= 1e-9 * np.abs(gwo).max(), int(np.argmax(np.abs(gw - gwo)))
+    assert np.abs(gL - gLo).max() <= 1e-9 * np.abs(gLo).max(), (gL, gLo)
 
 
 def test_adjoint_checkpoint_segments_agree(mcc):
