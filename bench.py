@@ -164,7 +164,7 @@ def bench_config(wl, layout: str, world: int) -> dict:
             "layout": layout + (" (segments by descending weight, the mcc_bin_weighted order)"
                                 if layout == "weight_ordered" else ""),
             "l2": f"no flush: {32 * wl.n / 1e9:.2g} GB of state read and written per step (129 MB L2)",
-            "parallelism": f"cells, {world} independent shard(s)"}
+            "parallelism": f"cells: {world} shard(s) of one problem (ShardedStep), diagnostics all-reduce"}
 
 
 def cpu_baseline(wl, budget_s: float = 15.0, one_thread: bool = False):
@@ -474,12 +474,27 @@ def run_ours(args):
     pairs = wl.pairs_per_step()
     species = list(zip(wl.q.tolist(), wl.m.tolist()))
     max_cell = int(wl.counts.sum(axis=1).max())
-    off = torch.from_numpy(wl.offsets).to(dev)
-    w = torch.from_numpy(wl.w).to(dev)
-    v = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (wl.vx, wl.vy, wl.vz)]
+    params = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
+    sharded = None
+    if world > 1:
+        # one global problem of world x C cells (rank r's block generated with its own seed), split by the
+        # product's ShardedStep: rank r owns cells [r C, (r + 1) C), steps them with cell_base = r C, and the
+        # per-species diagnostics are all-reduced after the timed steps
+        from paper_2407_19151_gb300 import workloads as W
+        from paper_2407_19151_gb300.sharding import ShardedStep
+        counts = np.concatenate([W.three_species_counts(args.cells, data_seed=1239 + 1000 * r) for r in range(world)])
+        goff = np.zeros(counts.size + 1, dtype=np.int64)
+        np.cumsum(counts.ravel(), out=goff[1:])
+        sharded = ShardedStep(goff, C * world, S, species, wl.lnL, params, max_cell=max_cell,
+                              cell_range=(rank * C, (rank + 1) * C)).load(wl.vx, wl.vy, wl.vz, wl.w, local=True)
+        params = sharded.params
+        v, w, off = sharded.state["v"], sharded.state["w"], sharded.state["offsets"]
+    else:
+        off = torch.from_numpy(wl.offsets).to(dev)
+        w = torch.from_numpy(wl.w).to(dev)
+        v = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (wl.vx, wl.vy, wl.vz)]
     corr = torch.zeros(C, dtype=torch.int32, device=dev)
     fail = torch.zeros(C, dtype=torch.int32, device=dev)
-    params = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
 
     def step(k0, nsteps=1):
         params.step = k0
@@ -528,10 +543,14 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     class_ms = np.array([[ev[2 * c].elapsed_time(ev[2 * c + 1]) for c in range(mcc.GROUP_CLASSES + 1)]
                          for ev in events]).mean(axis=0)
+    diagnostics = None
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
+        diag, _ = sharded.diagnostics()  # the all-reduce of the per-species sums over the ranks
+        diagnostics = {"particles": int(diag[:, 5].sum()), "weight": [float(x) for x in diag[:, 0]],
+                       "kinetic_energy": [float(x) for x in diag[:, 4]]}
         torch.distributed.barrier()
     mcc.sync_status(local)
     ms_step = ms / args.steps
@@ -556,7 +575,7 @@ def run_ours(args):
         host = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (wl.vx, wl.vy, wl.vz)]
         host_w = torch.from_numpy(wl.w).pin_memory()
         e2e_steps = max(2, min(args.steps, 5))
-        hp = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=1000)
+        hp = mcc.Params(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=1000, cell_base=params.cell_base)
         step_host(*host, host_w, wl.offsets, C, S, species, wl.lnL, hp, n_steps=1, max_cell=max_cell,
                   chunks=args.e2e_chunks, device=local)
         torch.cuda.synchronize(dev)
@@ -625,6 +644,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": graph_launches,  # one persistent step kernel per captured step + the cell-order kernel
         "correction_failures": fails,
+        "sharded_diagnostics": diagnostics,
         "fp64_step": fp64,
         "adjoint": adj,
         "binning": binning,

@@ -210,6 +210,24 @@ int mcc_bin_weighted(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, 
 int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells, int32_t n_species,
                    int32_t* perm_out, int64_t* offsets_out, mcc_stream stream);
 
+/*
+ * Per-species moments of a binned state, the diagnostics a sharded run sums over its ranks once per step (cells are
+ * independent within a step, Sec. 2, so the ranks exchange nothing else). For each species s, out[6 s + k]:
+ *   k = 0  sum w_p                 k = 1..3  sum m_s w_p v_p (component k - 1)
+ *   k = 4  sum of the kinetic energy, m_s w_p |v_p|^2 / 2 (relativistic: m_s w_p c^2 (gamma_p - 1), v_p the proper
+ *          velocity, gamma_p = sqrt(1 + |v_p|^2 / c^2))
+ *   k = 5  the number of particles
+ * and out[6 n_species] = sum over cells of fail_count (0 when fail_count is NULL).
+ *   offsets       [n_cells * n_species + 1] device int64 segment offsets (cell-major)
+ *   fail_count    [n_cells] device int32 or NULL (as accumulated by mcc_step_fused)
+ *   out           [6 n_species + 1] device doubles, overwritten (cleared on the stream first)
+ * Sums in FP64; partial sums are combined with double atomics, so the rounding of the result may differ between
+ * runs. Errors: MCC_ERR_INVALID_ARG for a bad argument or species mass, MCC_ERR_CUDA for a launch failure.
+ */
+int mcc_species_moments(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* offsets, int32_t n_cells,
+                        int32_t n_species, const mcc_species* sp, int32_t relativistic, double c,
+                        const int32_t* fail_count, double* out, mcc_stream stream);
+
 /* Gather a double or float array through perm: out[k] = in[perm[k]] (elem_bytes 4 or 8). */
 int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream);
 

@@ -13,7 +13,7 @@ from .pic import PicLoop
 from ._binding import (F32_MIXED, F64, FAIL_ERROR, FAIL_MOMENTUM_ONLY, FAIL_ROLLBACK, GROUP_CLASSES, N97, TA77,
                        Context, MccError, Params, context, default_interactions, lib, mcc_bin, mcc_bin_static,
                        mcc_adjoint, mcc_bin_weighted, mcc_correct, mcc_gather, mcc_gather_n, mcc_push,
-                       mcc_pair, mcc_scatter, mcc_step_fused, sync_status)
+                       mcc_pair, mcc_scatter, mcc_species_moments, mcc_step_fused, sync_status)
 
 
 def build(force: bool = False) -> str:
@@ -24,6 +24,6 @@ def build(force: bool = False) -> str:
 __all__ = [
     "build", "lib_path", "lib", "context", "Context", "Params", "MccError", "mcc_bin", "mcc_bin_static",
     "mcc_bin_weighted", "mcc_gather", "mcc_gather_n", "mcc_push", "PicLoop", "mcc_adjoint", "collision_steps", "mcc_pair",
-    "mcc_scatter", "mcc_correct", "mcc_step_fused", "sync_status", "default_interactions", "TA77", "N97", "F64",
+    "mcc_scatter", "mcc_correct", "mcc_species_moments", "mcc_step_fused", "sync_status", "default_interactions", "TA77", "N97", "F64",
     "F32_MIXED", "GROUP_CLASSES", "FAIL_ROLLBACK", "FAIL_MOMENTUM_ONLY", "FAIL_ERROR", "autotune",
 ]

@@ -125,6 +125,8 @@ def lib():
         "mcc_bin_weighted": (C.c_int, [vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t,
                                        vp]),
         "mcc_gather": (C.c_int, [vp, vp, C.c_int64, C.c_int32, vp, vp]),
+        "mcc_species_moments": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), C.c_int32,
+                                          C.c_double, vp, vp, vp]),
         "mcc_gather_n": (C.c_int, [P(vp), P(vp), P(C.c_int32), C.c_int32, vp, C.c_int64, vp]),
         "mcc_push": (C.c_int, [P(_Particles), vp, vp, vp, P(_Grid), C.c_double, C.c_int32, C.c_double, vp, vp]),
         "mcc_bin_static": (C.c_int, [vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp]),
@@ -317,6 +319,20 @@ def mcc_bin_static(cell: torch.Tensor, species: torch.Tensor, n_cells: int, n_sp
         _check(lib().mcc_bin_static(_ptr(cell), _ptr(species), n, n_cells, n_species, _ptr(perm), _ptr(offsets),
                                     _stream(stream, cell.device)), "mcc_bin_static")
     return perm, offsets
+
+
+def mcc_species_moments(vx, vy, vz, w, offsets, n_cells: int, n_species: int, species, relativistic: bool = False,
+                        c: float = 1.0, fail_count=None, out=None, stream=None) -> torch.Tensor:
+    """Per-species (sum w, sum m w v (3), kinetic energy, count) and the total of fail_count, as a float64 device
+    tensor of 6 n_species + 1 entries (see include/mcc.h)."""
+    ctx = context(vx.device)
+    P = _particles(vx, vy, vz, w)
+    if out is None:
+        out = torch.empty(6 * n_species + 1, dtype=torch.float64, device=vx.device)
+    _check(lib().mcc_species_moments(ctx.handle, C.byref(P), _ptr(offsets), int(n_cells), int(n_species),
+                                     _species(species), int(bool(relativistic)), float(c), _ptr(fail_count),
+                                     _ptr(out), _stream(stream, vx.device)), "mcc_species_moments")
+    return out
 
 
 def mcc_gather(x: torch.Tensor, perm: torch.Tensor, stream=None) -> torch.Tensor:

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["mcc_abi.cu", "mcc_cell.cu", "mcc_bin.cu", "mcc_adjoint.cu", "mcc_pic.cu", "mcc_group_f32.cu",
-           "mcc_group_f32rel.cu"]
+           "mcc_group_f32rel.cu", "mcc_moments.cu"]
 HEADERS = ["mcc_device.cuh", "mcc_kernels.h", "mcc_pic.h", "mcc_group.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

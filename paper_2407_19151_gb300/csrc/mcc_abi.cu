@@ -376,6 +376,29 @@ int mcc_bin_static(const int32_t* cell, const int32_t* species, int64_t n, int32
                                               S(stream)));
 }
 
+int mcc_species_moments(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells,
+                        int32_t n_species, const mcc_species* sp, int32_t relativistic, double c,
+                        const int32_t* fail_count, double* out, mcc_stream stream)
+{
+    if (!ctx || !P || !offsets || !sp || !out || n_cells < 0 || n_species < 1 || n_species > MCC_MAX_SPECIES)
+        return MCC_ERR_INVALID_ARG;
+    if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
+    if (P->n > 0 && (!P->vx || !P->vy || !P->vz || !P->w)) return MCC_ERR_INVALID_ARG;
+    if (relativistic && !(c > 0.0 && std::isfinite(c))) return MCC_ERR_INVALID_ARG;
+    mcc::SpeciesConst sc;
+    for (int s = 0; s < MCC_MAX_SPECIES; ++s) sc.m[s] = 0.0;
+    for (int s = 0; s < n_species; ++s) {
+        if (!(sp[s].m > 0.0) || !std::isfinite(sp[s].m)) return MCC_ERR_INVALID_ARG;
+        sc.m[s] = sp[s].m;
+    }
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = mcc::launch_species_moments(P->prec == MCC_F32_MIXED, P->vx, P->vy, P->vz, P->w, offsets,
+                                                      n_cells, n_species, sc, relativistic != 0, c, fail_count, out,
+                                                      ctx->num_sms, S(stream));
+    ctx->launches += 1;
+    return cuda_status(e);
+}
+
 int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_bytes, void* out, mcc_stream stream)
 {
     if (n < 0 || (elem_bytes != 4 && elem_bytes != 8) || (n > 0 && (!in || !perm || !out))) return MCC_ERR_INVALID_ARG;

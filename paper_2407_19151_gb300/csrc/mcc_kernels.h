@@ -128,4 +128,13 @@ cudaError_t launch_adjoint(const StepArgs& a, double lnL, double* ox, double* oy
                            int grid, cudaStream_t st);
 cudaError_t launch_gather(const void* in, const int32_t* perm, int64_t n, int elem_bytes, void* out, cudaStream_t st);
 
+// Species masses for the per-species moments (mcc_species_moments).
+struct SpeciesConst {
+    double m[kMaxSpecies];
+};
+cudaError_t launch_species_moments(bool f32, const void* vx, const void* vy, const void* vz, const double* w,
+                                   const int64_t* offsets, int32_t n_cells, int32_t S, const SpeciesConst& sc,
+                                   int rel, double c, const int32_t* fail_count, double* out, int num_sms,
+                                   cudaStream_t st);
+
 }  // namespace mcc

@@ -249,14 +249,24 @@ def differentiable(n_cells: int = 1024, per_species: int = 256, data_seed: int =
                     counts, vx, vy, vz, w, dt, method=N97, precision=precision, n_steps=steps, seed=0x5EED0004)
 
 
-def three_species(n_cells: int = 1 << 18, mean_count: float = 512.0, sigma: float = 0.5, data_seed: int = 1239,
-                  steps: int = 100, precision: str = "f32", method: int = N97) -> Workload:
-    rng = np.random.default_rng(data_seed)
+def _three_species_counts(rng, n_cells: int, mean_count: float, sigma: float) -> np.ndarray:
     mu = np.log(mean_count) - 0.5 * sigma * sigma
     tot = np.maximum(1, np.rint(np.exp(rng.normal(mu, sigma, n_cells)))).astype(np.int64)
     base = tot // 3
     rem = tot % 3
-    counts = np.stack([base + (rem > 0), base + (rem > 1), base], axis=1).astype(np.int64)
+    return np.stack([base + (rem > 0), base + (rem > 1), base], axis=1).astype(np.int64)
+
+
+def three_species_counts(n_cells: int = 1 << 18, mean_count: float = 512.0, sigma: float = 0.5,
+                         data_seed: int = 1239) -> np.ndarray:
+    """The (n_cells, 3) particle counts of three_species with the same arguments, without drawing the particles."""
+    return _three_species_counts(np.random.default_rng(data_seed), n_cells, mean_count, sigma)
+
+
+def three_species(n_cells: int = 1 << 18, mean_count: float = 512.0, sigma: float = 0.5, data_seed: int = 1239,
+                  steps: int = 100, precision: str = "f32", method: int = N97) -> Workload:
+    rng = np.random.default_rng(data_seed)
+    counts = _three_species_counts(rng, n_cells, mean_count, sigma)
     Te, Ti = 1.0, 0.5
     dtype = np.float32 if precision == "f32" else np.float64
     vx, vy, vz, w = _fill(rng, counts, [(Te, 1.0, (0, 0, 0), 0.0, 4.0), (Ti, M_PROTON, (0, 0, 0), 0.0, 4.0),
