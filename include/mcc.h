@@ -350,10 +350,11 @@ int mcc_set_tile_cap(mcc_ctx* ctx, int32_t cap);
 
 /* Size classes of mcc_step_fused's group kernels: class k (k = 0..4) runs groups of 32 << k threads and takes the
  * cells of at most caps[k] particles (the smallest such k); cells above caps[4] run on the one-CTA kernel.
- * particles_per_warp sets caps[k] = particles_per_warp << k (each capped by what one CTA's shared memory holds, 44
- * bytes per particle); 0 = automatic: the capacity with which sixteen warps share an SM's shared memory, and caps[4]
- * as large as one CTA's shared memory allows. Used by the autotuner. */
-int mcc_set_group_capacity(mcc_ctx* ctx, int32_t particles_per_warp);
+ * particles_per_warp sets caps[k] = particles_per_warp << k for k < 4 (0 = automatic: the capacity with which
+ * sixteen warps share an SM's shared memory); largest sets caps[4] (0 = as large as one CTA's shared memory
+ * allows). Every capacity is capped by what one CTA's shared memory holds (44 bytes per particle). Both 0 is the
+ * default. Used by the autotuner; the step's results do not depend on it. */
+int mcc_set_group_capacity(mcc_ctx* ctx, int32_t particles_per_warp, int32_t largest);
 
 /* The five class capacities mcc_step_fused uses for this precision and mode (caps_out: host int32[5]). */
 int mcc_group_capacities(mcc_ctx* ctx, int32_t prec, int32_t relativistic, int32_t* caps_out);

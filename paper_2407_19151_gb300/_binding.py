@@ -141,7 +141,7 @@ def lib():
                                      P(C.c_int32), C.c_int32, P(_Params), C.c_int32, C.c_int32, vp, vp, vp,
                                      C.c_size_t, vp]),
         "mcc_set_tile_cap": (C.c_int, [vp, C.c_int32]),
-        "mcc_set_group_capacity": (C.c_int, [vp, C.c_int32]),
+        "mcc_set_group_capacity": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "mcc_group_capacities": (C.c_int, [vp, C.c_int32, C.c_int32, P(C.c_int32)]),
         "mcc_sync_status": (C.c_int, [vp, vp]),
         "mcc_launch_count": (C.c_int64, [vp]),
@@ -196,8 +196,9 @@ class Context:
     def set_tile_cap(self, cap: int):
         _check(lib().mcc_set_tile_cap(self.handle, int(cap)), "mcc_set_tile_cap")
 
-    def set_group_capacity(self, particles_per_warp: int):
-        _check(lib().mcc_set_group_capacity(self.handle, int(particles_per_warp)), "mcc_set_group_capacity")
+    def set_group_capacity(self, particles_per_warp: int, largest: int = 0):
+        _check(lib().mcc_set_group_capacity(self.handle, int(particles_per_warp), int(largest)),
+               "mcc_set_group_capacity")
 
     def group_capacities(self, prec: int = F32_MIXED, relativistic: bool = False) -> list[int]:
         caps = (C.c_int32 * GROUP_CLASSES)()

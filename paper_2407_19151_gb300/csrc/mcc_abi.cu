@@ -4,11 +4,22 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mcc.h"
 #include "mcc_kernels.h"
 #include "mcc_pic.h"
 
 static_assert(mcc::kGroupClasses == MCC_GROUP_CLASSES, "size classes of the ABI and the kernels");
+
+// NVTX range over one entry point (header-only NVTX v3: a no-op unless a profiler injects itself), so that a timeline
+// shows each library call on the host thread that issued it.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct mcc_ctx {
     int device;
@@ -19,6 +30,7 @@ struct mcc_ctx {
     size_t smem_per_sm;
     int32_t tile_cap;  // particles staged on chip per cell by the one-CTA kernel; 0 = automatic
     int32_t group_cap; // particles per warp of the group kernels' size classes; 0 = automatic
+    int32_t group_top; // upper bound of the largest class; 0 = what one CTA's shared memory holds
     size_t smem_reserved;  // shared memory the system reserves per CTA
 };
 
@@ -28,6 +40,7 @@ namespace mcc {
 // stored as f = ln(A s) and h df/dx at x = ln s, where df/dx = 1 + s e^-s / (A G'(A)) by implicit
 // differentiation, G'(A) = -(1/A^2 - 1/sinh^2 A).
 namespace {
+
 void laurent(double A, double& L, double& dL)
 {
     // coth A - 1/A = sum_n 2^{2n} B_{2n} A^{2n-1} / (2n)!, for A < 1/2
@@ -280,6 +293,7 @@ int mcc_create(mcc_ctx** out, int device)
     c->launches = 0;
     c->tile_cap = 0;
     c->group_cap = 0;
+    c->group_top = 0;
     int optin = 0, sms = 0, per_sm = 0, reserved = 0;
     cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
     c->smem_reserved = (size_t)reserved;
@@ -330,6 +344,7 @@ int mcc_bin_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t
 int mcc_bin(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, int64_t n, int32_t n_cells,
             int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws, size_t ws_bytes, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_bin");
     if (!ctx || n < 0 || n_cells <= 0 || n_species <= 0 || !offsets_out) return MCC_ERR_INVALID_ARG;
     if (n > 0 && (!cell || !species || !perm_out)) return MCC_ERR_INVALID_ARG;
     if (n > INT32_MAX) return MCC_ERR_TOO_LARGE;
@@ -350,6 +365,7 @@ int mcc_bin_weighted(mcc_ctx* ctx, const int32_t* cell, const int32_t* species, 
                      int32_t n_cells, int32_t n_species, int32_t* perm_out, int64_t* offsets_out, void* ws,
                      size_t ws_bytes, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_bin_weighted");
     if (!ctx || n < 0 || n_cells <= 0 || n_species <= 0 || !offsets_out) return MCC_ERR_INVALID_ARG;
     if (n > 0 && (!cell || !species || !w || !perm_out)) return MCC_ERR_INVALID_ARG;
     if (n > INT32_MAX) return MCC_ERR_TOO_LARGE;
@@ -380,6 +396,7 @@ int mcc_species_moments(mcc_ctx* ctx, const mcc_particles* P, const int64_t* off
                         int32_t n_species, const mcc_species* sp, int32_t relativistic, double c,
                         const int32_t* fail_count, double* out, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_species_moments");
     if (!ctx || !P || !offsets || !sp || !out || n_cells < 0 || n_species < 1 || n_species > MCC_MAX_SPECIES)
         return MCC_ERR_INVALID_ARG;
     if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
@@ -408,6 +425,7 @@ int mcc_gather(const void* in, const int32_t* perm, int64_t n, int32_t elem_byte
 int mcc_gather_n(const void* const* in, void* const* out, const int32_t* elem_bytes, int32_t n_arrays,
                  const int32_t* perm, int64_t n, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_gather_n");
     if (n < 0 || n_arrays < 1 || n_arrays > MCC_MAX_GATHER || !in || !out || !elem_bytes) return MCC_ERR_INVALID_ARG;
     for (int j = 0; j < n_arrays; ++j) {
         if (elem_bytes[j] != 4 && elem_bytes[j] != 8) return MCC_ERR_INVALID_ARG;
@@ -420,6 +438,7 @@ int mcc_gather_n(const void* const* in, void* const* out, const int32_t* elem_by
 int mcc_push(const mcc_particles* P, void* x, void* y, void* z, const mcc_grid* grid, double dt,
              int32_t relativistic, double c, int32_t* cell_out, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_push");
     if (!P || !grid || P->n < 0 || (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED)) return MCC_ERR_INVALID_ARG;
     if (relativistic != 0 && relativistic != 1) return MCC_ERR_INVALID_ARG;
     const int32_t nc[3] = {grid->nx, grid->ny, grid->nz};
@@ -446,6 +465,7 @@ int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_sp
              int32_t inter, uint64_t seed, uint64_t step, int32_t* pair_i, int32_t* pair_j, uint8_t* pair_flags,
              mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_pair");
     if (!ctx || !offsets || !pair_i || !pair_j || !pair_flags || inter < 0 || inter > 0xFFFFFF)
         return MCC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
@@ -470,6 +490,7 @@ int mcc_scatter(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
                 const int32_t* pair_j, const uint8_t* pair_flags, const mcc_params* p, void* backup,
                 mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_scatter");
     if (!ctx || !P || !offsets || !sp || !lnL || !pair_i || !pair_j || !pair_flags || !backup || !valid_params(p) ||
         inter < 0 || inter > 0xFFFFFF || p->pairing != 0)
         return MCC_ERR_INVALID_ARG;
@@ -493,6 +514,7 @@ int mcc_correct(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
                 const mcc_species* sp, int32_t sa, int32_t sb, int32_t inter, const mcc_params* p,
                 const void* backup, int32_t* corr_pairs_out, int32_t* fail_flags_out, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_correct");
     if (!ctx || !P || !offsets || !sp || !backup || !valid_params(p) || inter < 0 || inter > 0xFFFFFF)
         return MCC_ERR_INVALID_ARG;
     if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
@@ -557,7 +579,8 @@ void group_caps(const mcc_ctx* ctx, bool f32, bool rel, int32_t caps[mcc::kGroup
         const size_t st = group_static_smem(f32, rel, k);
         const size_t maxp = ctx->smem_optin > st ? (ctx->smem_optin - st) / mcc::kGroupBytesPerParticle : 0;
         size_t cap = per_warp << k;
-        if (cap > maxp || (k == mcc::kGroupClasses - 1 && ctx->group_cap == 0)) cap = maxp;
+        if (k == mcc::kGroupClasses - 1) cap = ctx->group_top > 0 ? (size_t)ctx->group_top : maxp;
+        if (cap > maxp) cap = maxp;
         if (cap > 65535) cap = 65535;  // cell-local indices are 16-bit
         caps[k] = (int32_t)cap;
     }
@@ -584,10 +607,11 @@ int mcc_step_workspace_size(mcc_ctx* ctx, int32_t prec, int32_t n_cells, int32_t
     return MCC_OK;
 }
 
-int mcc_set_group_capacity(mcc_ctx* ctx, int32_t particles_per_warp)
+int mcc_set_group_capacity(mcc_ctx* ctx, int32_t particles_per_warp, int32_t largest)
 {
-    if (!ctx || particles_per_warp < 0) return MCC_ERR_INVALID_ARG;
+    if (!ctx || particles_per_warp < 0 || largest < 0) return MCC_ERR_INVALID_ARG;
     ctx->group_cap = particles_per_warp;
+    ctx->group_top = largest;
     return MCC_OK;
 }
 
@@ -604,6 +628,7 @@ int mcc_step_fused(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets,
                    const mcc_params* p, int32_t n_steps, int32_t max_cell, int32_t* corr_pairs, int32_t* fail_count,
                    void* ws, size_t ws_bytes, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_step_fused");
     if (!ctx || !P || !offsets || !sp || !lnL || !interactions || !valid_params(p) || n_steps < 0 || max_cell < 0)
         return MCC_ERR_INVALID_ARG;
     if (P->prec != MCC_F64 && P->prec != MCC_F32_MIXED) return MCC_ERR_INVALID_ARG;
@@ -723,6 +748,7 @@ int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
                 int32_t max_cell, double* vx_out, double* vy_out, double* vz_out, double* gvx, double* gvy,
                 double* gvz, double* gw, double* glnL, void* ws, size_t ws_bytes, mcc_stream stream)
 {
+    NvtxRange nvtx_("mcc_adjoint");
     if (!ctx || !P || !offsets || !sp || !lnL || !valid_params(p) || inter < 0 || inter > 0xFFFFFF || max_cell < 0)
         return MCC_ERR_INVALID_ARG;
     if (max_cell > MCC_MAX_SEGMENT) return MCC_ERR_TOO_LARGE;

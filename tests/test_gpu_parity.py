@@ -330,7 +330,7 @@ def test_fused_cells_above_every_class(mcc):
     formed from float-stored velocities)."""
     wl = W.three_species(n_cells=40, mean_count=300)
     ctx = mcc.context(0)
-    ctx.set_group_capacity(16)
+    ctx.set_group_capacity(16, 256)
     ctx.set_tile_cap(128)
     try:
         assert ctx.group_capacities(mcc.F32_MIXED)[-1] == 256
