@@ -20,8 +20,9 @@
 // Precision: the velocity state of the cell visit is float-float (hi + lo, ~48 bits) in shared memory and is rounded
 // to float once, at write-back. The pair kinematics (relative velocity, scattering length, angle, rotation) run in
 // float on that state; every per-cell sum, the coefficients B, Delta E, Delta E_s, the energy-pair caps and their
-// prefix sums and the non-relativistic energy pairs run in float-float. Relativistic energy pairs, and relativistic
-// scatter pairs whose centre-of-momentum frame moves with gamma_C > 2, run in double on the exact state.
+// prefix sums and the energy pairs run in float-float. Relativistic scatter pairs whose centre-of-momentum frame moves
+// with gamma_C > 2, and the energy caps of pairs with a particle at gamma > 2, form their cancelling differences in
+// float-float.
 //
 // Per-species momentum m_s sum w v and energy m_s sum w KE/m are computed once at the cell load and carried through
 // the interactions: the scatter changes them, the momentum shift restores the interaction's total (its change to a
@@ -603,24 +604,133 @@ __device__ __forceinline__ void rel_dp(const StepArgs& A, V kappa, const RelCM<V
     dp[2] = dz + coef_b * Vd * cm.Vz;
 }
 
-// The double-precision relativistic pair (from the exact state) for a fast-moving CM frame; out of line (rare).
-static __device__ __noinline__ void rel_pair_f64(const StepArgs& A, const InterConst& ic, const double ui[3],
-                                                 const double uj[3], double wf, uint8_t f, uint4 r, double dvi[3],
-                                                 double dvj[3])
+// ----------------------------------------------------------------------------------------------- fast relativistic
+// Float-float relativistic kinematics for the pairs whose CM frame (gamma_C > 2) or particles (gamma > 2) move fast.
+// In float the cancellations of gamma_j du - (gamma_i - gamma_j) u_j (the CM momentum of co-moving particles) and of
+// gamma_rel - 1 = (|du|^2 / c^2 - (gamma_i - gamma_j)^2) / 2 lose ~gamma^2 of the precision; formed in float-float
+// (about 2^-44) they keep ~2^-37 at gamma = 10, and the rest of the pair's kinematics has no cancellation left.
+
+__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3])
 {
-    const double ma = A.ma[ic.a], mb = A.ma[ic.b];
-    const double du[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
-    const RelCM<double> cm = rel_cm_du<double>(A.c, ma, mb, ui, uj, du);
-    if (!(cm.pmag > 0.0)) {
-        dvi[0] = dvi[1] = dvi[2] = dvj[0] = dvj[1] = dvj[2] = 0.0;
-        return;
-    }
-    double dp[3];
-    rel_dp<double>(A, ic.kappa, cm, A.c, wf, f, u23<double>(r.x), u23<double>(r.y), u23<double>(r.w), dp);
+    return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
+
+// gamma of each particle, the difference du = u1 - u2, |du|^2 and gamma1 - gamma2 = du . (u1 + u2) / (c^2 (g1 + g2)).
+struct RelFF {
+    ff g1, g2, du[3], du2, dg;
+};
+__device__ __forceinline__ void rel_ff(ff c2inv, const ff u1[3], const ff u2[3], RelFF& r)
+{
+    const ff one = ffk(1.f);
+    r.g1 = ffq_sqrt(ff_add(one, ff_mul(ff_dot3(u1, u1), c2inv)));
+    r.g2 = ffq_sqrt(ff_add(one, ff_mul(ff_dot3(u2, u2), c2inv)));
+    ff su[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        dvi[d] = dp[d] / ma;
-        dvj[d] = -dp[d] / mb;
+        r.du[d] = ff_sub(u1[d], u2[d]);
+        su[d] = ff_add(u1[d], u2[d]);
+    }
+    r.du2 = ff_dot3(r.du, r.du);
+    r.dg = ffq_div(ff_mul(ff_dot3(r.du, su), c2inv), ff_add(r.g1, r.g2));
+}
+// gamma_rel - 1 (clamped at 0)
+__device__ __forceinline__ ff rel_ff_grm1(const RelFF& r, ff c2inv)
+{
+    const ff x = ff_sub(ff_mul(r.du2, c2inv), ff_mul(r.dg, r.dg));
+    return x.hi > 0.f ? ff{0.5f * x.hi, 0.5f * x.lo} : ffk(0.f);
+}
+
+// The CM frame of a relativistic pair (the quantities of rel_cm_du) with the CM momentum formed in float-float.
+__device__ __forceinline__ RelCM<float> rel_cm_ff(float cc, ff c2inv, float ma, float mb, const ff ui[3],
+                                                  const ff uj[3])
+{
+    RelFF r;
+    rel_ff(c2inv, ui, uj, r);
+    RelCM<float> o;
+    const float gi = ff_round(r.g1), gj = ff_round(r.g2);
+    const float M = ma * gi + mb * gj;
+    const float Mr = 1.f / M;
+    o.Vx = (ma * ff_round(ui[0]) + mb * ff_round(uj[0])) * Mr;
+    o.Vy = (ma * ff_round(ui[1]) + mb * ff_round(uj[1])) * Mr;
+    o.Vz = (ma * ff_round(ui[2]) + mb * ff_round(uj[2])) * Mr;
+    const float grm1 = ff_round(rel_ff_grm1(r, c2inv));
+    const float Minv = sqrtf((ma + mb) * (ma + mb) + 2.f * ma * mb * grm1);
+    o.gC = M / Minv;
+    const float coef_b = o.gC * o.gC / (cc * cc * (o.gC + 1.f));
+    const float k = ma * mb * Mr;
+    float q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q[d] = k * ff_round(ff_sub(ff_mul(r.g2, r.du[d]), ff_mul(r.dg, uj[d])));
+    const float Vq = o.Vx * q[0] + o.Vy * q[1] + o.Vz * q[2];
+    o.px = q[0] + coef_b * Vq * o.Vx;
+    o.py = q[1] + coef_b * Vq * o.Vy;
+    o.pz = q[2] + coef_b * Vq * o.Vz;
+    const float p2 = o.px * o.px + o.py * o.py + o.pz * o.pz;
+    o.pmag = sqrtf(p2);
+    const float gsa = sqrtf(1.f + p2 / (ma * ma * cc * cc)), gsb = sqrtf(1.f + p2 / (mb * mb * cc * cc));
+    o.vrel = o.pmag * (1.f / (ma * gsa) + 1.f / (mb * gsb));
+    return o;
+}
+
+// Centre-of-mass kinetic energy of a weighted relativistic pair (weighted masses m1, m2), float-float inputs:
+// KE_cm = 2 m1 m2 c^2 (gamma_rel - 1) / (E_cm / c^2 + m1 + m2).
+__device__ __forceinline__ float pair_kecm_ff(float cc, ff c2inv, float m1, float m2, const ff u1[3], const ff u2[3])
+{
+    RelFF r;
+    rel_ff(c2inv, u1, u2, r);
+    const float grm1 = ff_round(rel_ff_grm1(r, c2inv));
+    const float Minv = sqrtf((m1 + m2) * (m1 + m2) + 2.f * m1 * m2 * grm1);
+    return 2.f * m1 * m2 * cc * cc * grm1 / (Minv + m1 + m2);
+}
+
+// Appendix A energy pair in float-float: p1' = p1 + alpha du, p2' = p2 - alpha du with the pair's total energy
+// lowered by U, alpha the root of smaller magnitude of a alpha^2 + b alpha + c0 = 0 (the coefficients of
+// energy_pair<., true>, cancellation-free forms). Masses and U are taken in units of m1 + m2 (the quadratic is
+// homogeneous of degree one in them: alpha scales with the masses), which keeps b^2 and c0 inside float's range.
+// Updates u1, u2 (float-float) in place.
+__device__ __forceinline__ void energy_pair_rel_ff(ff c2inv, ff m1, ff m2, ff u1[3], ff u2[3], ff U)
+{
+    const ff M12 = ff_add(m1, m2);
+    const ff n1 = ffq_div(m1, M12), n2 = ffq_div(m2, M12);
+    RelFF r;
+    rel_ff(c2inv, u1, u2, r);
+    const ff E1 = ff_mul(n1, r.g1), E2 = ff_mul(n2, r.g2);
+    const ff Ut = ff_mul(ffq_div(U, M12), c2inv);
+    const ff A = ff_sub(ff_add(E1, E2), Ut);
+    const ff twoE1mU = ff_sub(ff_add(E1, E1), Ut), twoE2mU = ff_sub(ff_add(E2, E2), Ut);
+    const ff n12 = ff_mul(n1, n2);
+    ff bdot = ffk(0.f), ptdu = ffk(0.f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const ff pt = ff_add(ff_mul(n1, u1[d]), ff_mul(n2, u2[d]));
+        const ff x12 = ff_mul(n12, ff_sub(ff_mul(r.g2, r.du[d]), ff_mul(r.dg, u2[d])));
+        const ff bv = ff_sub(ff_mul(ff_add(A, A), ff_add(x12, ff_mul(Ut, ff_mul(n2, u2[d])))),
+                             ff_mul(ff_mul(Ut, twoE1mU), pt));
+        bdot = ff_add(bdot, ff_mul(r.du[d], bv));
+        ptdu = ff_add(ptdu, ff_mul(pt, r.du[d]));
+    }
+    const ff a = ff_mul_f(ff_sub(ff_mul(ff_mul(A, A), ff_mul(r.du2, c2inv)), ff_mul(ff_mul(ptdu, ptdu), ff_mul(c2inv, c2inv))),
+                          4.f);
+    const ff b = ff_mul_f(ff_mul(c2inv, bdot), 4.f);
+    // c0 = Ut (2 E1 - Ut) (2 E2 - Ut) (2 E1 + 2 E2 - Ut)
+    const ff c0 = ff_mul(ff_mul(Ut, twoE1mU), ff_mul(twoE2mU, ff_add(ff_add(twoE1mU, twoE2mU), Ut)));
+    ff disc = ff_sub(ff_mul(b, b), ff_mul_f(ff_mul(a, c0), 4.f));
+    if (!(disc.hi > 0.f)) disc = ffk(0.f);
+    const ff sq = ffq_sqrt(disc);
+    const ff q = ff_mul_f(b.hi >= 0.f ? ff_add(b, sq) : ff_sub(b, sq), -0.5f);
+    ff alpha = ffk(0.f);
+    if (q.hi != 0.f) {
+        alpha = ffq_div(c0, q);
+        if (a.hi != 0.f) {
+            const ff r1 = ffq_div(q, a);
+            if (ff_lt(ff_abs(r1), ff_abs(alpha))) alpha = r1;
+        }
+    }
+    const ff f1 = ffq_div(alpha, n1), f2 = ffq_div(alpha, n2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        u1[d] = ff_add(u1[d], ff_mul(f1, r.du[d]));
+        u2[d] = ff_sub(u2[d], ff_mul(f2, r.du[d]));
     }
 }
 
@@ -757,26 +867,15 @@ __device__ __forceinline__ void gscatter_pair(const StepArgs& A, const GTile& t,
         const float ki[3] = {ff_round(vi[0]), ff_round(vi[1]), ff_round(vi[2])};
         const float kj[3] = {ff_round(vj[0]), ff_round(vj[1]), ff_round(vj[2])};
         const RelCM<float> cm = rel_cm_du<float>(cc, ma, mb, ki, kj, du);
-        if (cm.gC > 2.f) {
-            // a fast-moving CM frame amplifies float rounding by ~gamma_C^2: this pair's kinematics run in double
-            const double di[3] = {ff_dbl(vi[0]), ff_dbl(vi[1]), ff_dbl(vi[2])};
-            const double dj[3] = {ff_dbl(vj[0]), ff_dbl(vj[1]), ff_dbl(vj[2])};
-            double ddi[3], ddj[3];
-            rel_pair_f64(A, ic, di, dj, (double)wf, f, r, ddi, ddj);
+        // a fast-moving CM frame amplifies float rounding by ~gamma_C^2: its CM momentum is formed in float-float
+        const RelCM<float> cmx = cm.gC > 2.f ? rel_cm_ff(cc, ff{A.c2inv_f, A.c2inv_lo}, ma, mb, vi, vj) : cm;
+        if (!(cmx.pmag > 0.f)) return;
+        float dp[3];
+        rel_dp<float>(A, ic.kappa_f, cmx, cc, wf, f, U1, U2, U4, dp);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                dvi[d] = (float)ddi[d];
-                dvj[d] = (float)ddj[d];
-            }
-        } else {
-            if (!(cm.pmag > 0.f)) return;
-            float dp[3];
-            rel_dp<float>(A, ic.kappa_f, cm, cc, wf, f, U1, U2, U4, dp);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                dvi[d] = dp[d] / ma;
-                dvj[d] = -dp[d] / mb;
-            }
+        for (int d = 0; d < 3; ++d) {
+            dvi[d] = dp[d] / ma;
+            dvj[d] = -dp[d] / mb;
         }
     }
     bool upd_i = true, upd_j = true;
@@ -921,7 +1020,7 @@ __device__ __forceinline__ ff ke_per_mass(const ff v[3], ff c2inv)
 // the crossing pair, which takes the remainder of |Delta E_s| (a prefix sum over the caps gives every pair the sum
 // of the caps before it). Non-relativistic pairs in float-float (Eqs. vp1_inelastic, vp2_inelastic, vrel_inelastic:
 // a capped pair has U / KE_cm = +-fE, so its g - 1 is a constant); relativistic pairs through the Appendix A
-// quadratic in double. Returns the absorbed energy (signed as D) and adds the pairs used to `used`; done = D was
+// quadratic in float-float. Returns the absorbed energy (signed as D) and adds the pairs used to `used`; done = D was
 // absorbed.
 template <bool REL, int WIDTH>
 __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc, int mode, ff D,
@@ -931,10 +1030,10 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
     const unsigned mask = WIDTH == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
     const int cap = t.cap;
     const ff ms = mass_ff(A, spc);
-    const double ms_d = A.m[spc];
     const ff fE = {A.fE_f, A.fE_lo};
     const ff gm1p = {A.gm1p_f, A.gm1p_lo};  // sqrt(1 - fE) - 1: a capped pair that loses energy
     const ff gm1n = {A.gm1n_f, A.gm1n_lo};  // sqrt(1 + fE) - 1: a capped pair that gains energy
+    const ff c2inv = {A.c2inv_f, A.c2inv_lo};
     const ff Dinit = ff_abs(D);
     ff Dabs = Dinit;
     const bool neg = D.hi < 0.f;
@@ -977,15 +1076,9 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
                         k2[d] = ff_round(v2[d]);
                         dk[d] = ff_diff(v1[d], v2[d]);
                     }
-                    float Kf;
-                    if (fast_pair(cc, k1, k2)) {
-                        const double d1[3] = {ff_dbl(v1[0]), ff_dbl(v1[1]), ff_dbl(v1[2])};
-                        const double d2[3] = {ff_dbl(v2[0]), ff_dbl(v2[1]), ff_dbl(v2[2])};
-                        Kf = (float)pair_kecm<double, true>(A.c, ms_d * A.w[cs + CHK(t.dbg, i, t.n)],
-                                                            ms_d * A.w[cs + CHK(t.dbg, j, t.n)], d1, d2);
-                    } else {
-                        Kf = pair_kecm_du<float>(cc, A.m_f[spc] * wi.x, A.m_f[spc] * wj.x, k1, k2, dk);
-                    }
+                    const float Kf = fast_pair(cc, k1, k2)
+                                         ? pair_kecm_ff(cc, c2inv, A.m_f[spc] * wi.x, A.m_f[spc] * wj.x, v1, v2)
+                                         : pair_kecm_du<float>(cc, A.m_f[spc] * wi.x, A.m_f[spc] * wj.x, k1, k2, dk);
                     K = ffk(Kf);
                     capx = ffk(Kf > 0.f ? A.fE_f * Kf : 0.f);
                 }
@@ -1014,14 +1107,12 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
                         t.v[d * cap + CHK(t.dbg, j, t.n)] = ff_st(ff_sub(v2[d], ff_mul(f2, vr[d])));
                     }
                 } else {
-                    double d1[3] = {ff_dbl(v1[0]), ff_dbl(v1[1]), ff_dbl(v1[2])};
-                    double d2[3] = {ff_dbl(v2[0]), ff_dbl(v2[1]), ff_dbl(v2[2])};
-                    energy_pair<double, true>(A.c, ms_d * A.w[cs + CHK(t.dbg, i, t.n)],
-                                              ms_d * A.w[cs + CHK(t.dbg, j, t.n)], 0.0, d1, d2, ff_dbl(U));
+                    const float2 wi = t.w[CHK(t.dbg, i, t.n)], wj = t.w[CHK(t.dbg, j, t.n)];
+                    energy_pair_rel_ff(c2inv, ff_mul(ms, ff{wi.x, wi.y}), ff_mul(ms, ff{wj.x, wj.y}), v1, v2, U);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        t.v[d * cap + CHK(t.dbg, i, t.n)] = ff_st(ff_from_double(d1[d]));
-                        t.v[d * cap + CHK(t.dbg, j, t.n)] = ff_st(ff_from_double(d2[d]));
+                        t.v[d * cap + CHK(t.dbg, i, t.n)] = ff_st(v1[d]);
+                        t.v[d * cap + CHK(t.dbg, j, t.n)] = ff_st(v2[d]);
                     }
                 }
                 ++used;
