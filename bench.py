@@ -164,7 +164,8 @@ def bench_config(wl, layout: str, world: int) -> dict:
             "layout": layout + (" (segments by descending weight, the mcc_bin_weighted order)"
                                 if layout == "weight_ordered" else ""),
             "l2": f"no flush: {32 * wl.n / 1e9:.2g} GB of state read and written per step (129 MB L2)",
-            "parallelism": f"cells: {world} shard(s) of one problem (ShardedStep), diagnostics all-reduce"}
+            "parallelism": (f"cells: one problem in {world} shards (ShardedStep), diagnostics all-reduce" if world > 1
+                            else "cells: one problem on one GPU")}
 
 
 def cpu_baseline(wl, budget_s: float = 15.0, one_thread: bool = False):

@@ -437,8 +437,9 @@ __device__ __forceinline__ void warp_sort_buf(uint64_t* buf, int n)
     __syncwarp();
 }
 
-// Energy-correction pairs of fast particles (gamma > 2 for either) run in double on the mixed path: the pair's
-// CM kinetic energy and the Appendix-A quadratic lose ~gamma^2 of float precision for co-moving particles.
+// Energy-correction pairs of fast particles (gamma > 2 for either) need more than float on the mixed path: the pair's
+// CM kinetic energy and the Appendix-A quadratic lose ~gamma^2 of float precision for co-moving particles (double in
+// the one-CTA kernel, float-float in the group kernels).
 template <class V>
 __device__ __forceinline__ bool fast_pair(V c, const V v1[3], const V v2[3])
 {
