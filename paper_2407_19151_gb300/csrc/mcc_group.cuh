@@ -389,13 +389,24 @@ __device__ void gpermutations(const StepArgs& A, const GTile& t, GShared<G>& sh,
     for (int side = 0; side < nside; ++side) {
         const int s0 = side ? b0 : a0, n = side ? nb : na, base = side ? B0 : 0, l = side ? lg1 : lg0;
         const uint32_t tag = side ? kTagPermB : kTagPermA;
-        for (int h = threadIdx.x; 2 * h < n; h += G) {
+        // two Philox blocks per thread and iteration: independent chains for the issue slots
+        for (int h = threadIdx.x; 2 * h < n; h += 2 * G) {
+            const int h2 = h + G;
             const uint4 r = draw_at(A.rng, step, (uint32_t)h, (uint32_t)c, ictr, tag);
+            const uint4 r2 = draw_at(A.rng, step, (uint32_t)h2, (uint32_t)c, ictr, tag);
             key[CHK(t.dbg, s0 + 2 * h, t.n)] = r.x;
             atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r.x >> (32 - l)) : 0), t.cap)], 1u);
             if (2 * h + 1 < n) {
                 key[CHK(t.dbg, s0 + 2 * h + 1, t.n)] = r.z;
                 atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r.z >> (32 - l)) : 0), t.cap)], 1u);
+            }
+            if (2 * h2 < n) {
+                key[CHK(t.dbg, s0 + 2 * h2, t.n)] = r2.x;
+                atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r2.x >> (32 - l)) : 0), t.cap)], 1u);
+                if (2 * h2 + 1 < n) {
+                    key[CHK(t.dbg, s0 + 2 * h2 + 1, t.n)] = r2.z;
+                    atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r2.z >> (32 - l)) : 0), t.cap)], 1u);
+                }
             }
         }
     }
@@ -465,25 +476,49 @@ __device__ __forceinline__ void sort_keys(uint64_t* key, int n)
 
 // Weight-descending order of each species, once per visit (optional step of Algorithm 1): a segment stored with
 // strictly increasing keys needs no order (mode 3); distinct keys fix the order for the visit (mode 0); all equal
-// make it the random permutation (mode 1); partial ties sort it per interaction (mode 2).
+// make it the random permutation (mode 1); partial ties sort it per interaction (mode 2). The species that need a
+// sort are sorted at once, species s by warp s mod (G / 32) (segments above the one-warp sort by the whole group,
+// one after another).
 template <int G>
 __device__ __noinline__ void gweight_order(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t cs, int S)
 {
+    constexpr int kWarps = G / 32;
+    const int warp = threadIdx.x >> 5;
+    unsigned need = 0;  // species whose segment is not stored in strictly descending weight
     for (int sp = 0; sp < S; ++sp) {
         const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
         bool bad = false;
         for (int q = threadIdx.x; q + 1 < ns; q += G)
             bad |= weight_key(A.w[cs + CHK(t.dbg, s0 + q, t.n)], 0) >=
                    weight_key(A.w[cs + CHK(t.dbg, s0 + q + 1, t.n)], 0);
-        if (!gany<G>(bad)) {
-            if (threadIdx.x == 0) sh.wmode[sp] = 3;
-            continue;
-        }
+        if (gany<G>(bad)) need |= 1u << sp;
+        else if (threadIdx.x == 0) sh.wmode[sp] = 3;
+    }
+    if (!need) return;
+    for (int sp = 0; sp < S; ++sp) {
+        if (!(need >> sp & 1u)) continue;
+        const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
         uint64_t* key = t.scr + s0;
         for (int q = threadIdx.x; q < ns; q += G)
             key[CHK(t.dbg, q, ns)] = weight_key(A.w[cs + CHK(t.dbg, s0 + q, t.n)], (uint32_t)q);
-        gsync<G>();
-        sort_keys<G>(key, ns);
+    }
+    gsync<G>();
+    for (int sp = 0; sp < S; ++sp) {  // one-warp sorts, spread over the warps
+        const int ns = sh.off[sp + 1] - sh.off[sp];
+        if ((need >> sp & 1u) && ns <= kWarpSortMax && warp == sp % kWarps) warp_sort_buf(t.scr + sh.off[sp], ns);
+    }
+    for (int sp = 0; sp < S; ++sp) {  // larger segments by the whole group
+        const int ns = sh.off[sp + 1] - sh.off[sp];
+        if ((need >> sp & 1u) && ns > kWarpSortMax) {
+            gsync<G>();
+            block_sort_u64(t.scr + sh.off[sp], ns);
+        }
+    }
+    gsync<G>();
+    for (int sp = 0; sp < S; ++sp) {
+        if (!(need >> sp & 1u)) continue;
+        const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
+        const uint64_t* key = t.scr + s0;
         bool tie = false;
         for (int q = threadIdx.x; q < ns; q += G) {
             t.rho[CHK(t.dbg, s0 + q, t.n)] = (uint16_t)(s0 + (int)(key[CHK(t.dbg, q, ns)] & kPermMask));
@@ -494,8 +529,8 @@ __device__ __noinline__ void gweight_order(const StepArgs& A, const GTile& t, GS
             const bool all_equal = (key[0] >> kPermBits) == (key[CHK(t.dbg, ns - 1, ns)] >> kPermBits);
             sh.wmode[sp] = all_equal ? 1 : (anytie ? 2 : 0);
         }
-        gsync<G>();
     }
+    gsync<G>();
 }
 
 // Energy-pair order of a segment with partially tied weights: the interaction's permutation stably sorted by
