@@ -372,9 +372,10 @@ def pic_measure(wl, dev, hbm, steps: int = 4):
 
 
 def adjoint_measure(dev):
-    """Differentiable step (1024 cells x 512 particles, two species of mass ratio 1836, FP64, N97): 50 steps with a
-    checkpoint every 10, gradient of the final per-species temperatures and drifts with respect to the initial
-    velocities, weights and Coulomb logarithms. Forward and backward timed separately with CUDA events."""
+    """Differentiable step (1024 cells x 512 particles, two species of mass ratio 1836, FP64, N97): 50 steps, gradient
+    of the final per-species temperatures and drifts with respect to the initial velocities, weights and Coulomb
+    logarithms, once with a checkpoint every 10 steps and once with recorded tapes. Forward and backward timed
+    separately with CUDA events."""
     import torch
 
     import paper_2407_19151_gb300 as mcc
@@ -400,27 +401,36 @@ def adjoint_measure(dev):
         return loss
 
     stream = torch.cuda.current_stream(dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, species, params, 2, checkpoint_every=every)
-    temps_drifts(out).backward()  # warm-up (library load, workspaces)
-    for x in (*v, w, L):
-        x.grad = None
-    torch.cuda.synchronize(dev)
-    ev[0].record(stream)
-    out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, species, params, n_steps,
-                              checkpoint_every=every)
-    loss = temps_drifts(out)
-    ev[1].record(stream)
-    loss.backward()
-    ev[2].record(stream)
-    torch.cuda.synchronize(dev)
-    f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     pairs = wl.pairs_per_step() * n_steps
-    return {"workload": "differentiable, 1024 cells x 512, two species, FP64, N97", "steps": n_steps,
-            "checkpoint_every": every, "forward_ms": f_ms, "backward_ms": b_ms,
-            "pairs_per_s_forward_backward": pairs / ((f_ms + b_ms) * 1e-3),
-            "grad_norms": {"v": float(sum(x.grad.norm() ** 2 for x in v) ** 0.5), "w": float(w.grad.norm()),
-                           "lnL": float(L.grad.norm())}}
+    res = {"workload": "differentiable, 1024 cells x 512, two species, FP64, N97", "steps": n_steps}
+    for mode, tape in (("checkpoint", False), ("tape", True)):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, species, params, 2, checkpoint_every=every,
+                                  tape=tape)
+        temps_drifts(out).backward()  # warm-up (library load, workspaces)
+        for x in (*v, w, L):
+            x.grad = None
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, species, params, n_steps,
+                                  checkpoint_every=every, tape=tape)
+        loss = temps_drifts(out)
+        ev[1].record(stream)
+        loss.backward()
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        res[mode] = {"forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
+                     "pairs_per_s_forward_backward": pairs / ((f_ms + b_ms) * 1e-3),
+                     "grad_norms": {"v": float(sum(x.grad.norm() ** 2 for x in v) ** 0.5),
+                                    "w": float(w.grad.norm()), "lnL": float(L.grad.norm())}}
+        for x in (*v, w, L):
+            x.grad = None
+        del out, loss
+    res["checkpoint"]["checkpoint_every"] = every
+    res["tape"]["tape_bytes"] = mcc.adjoint_tape_bytes(dev, wl.n_cells, int(wl.counts.sum(1).max()),
+                                                       params.max_corr_passes) * n_steps * 3
+    return res
 
 
 CLASS_KERNELS = [f"group_kernel<false, {32 << k}>" for k in range(5)] + ["cell_kernel<float, 0, 0>"]

@@ -123,9 +123,18 @@ typedef struct {
 int mcc_create(mcc_ctx** ctx, int device);
 void mcc_destroy(mcc_ctx* ctx);
 
-/* Bytes of device workspace mcc_adjoint needs for n_cells cells of at most max_cell particles. */
+/* Bytes of device workspace mcc_adjoint needs for n_cells cells of at most max_cell particles when it recomputes
+ * (tape = MCC_ADJOINT_RECOMPUTE: one working slab per resident CTA). */
 int mcc_adjoint_workspace_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, int32_t max_corr_passes,
                                size_t* bytes);
+
+/* Bytes of one recorded tape of one interaction (tape = MCC_ADJOINT_RECORD / MCC_ADJOINT_REPLAY: one slab per cell,
+ * about 250 bytes per particle of max_cell plus 80 bytes per possible energy pair). */
+int mcc_adjoint_tape_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, int32_t max_corr_passes, size_t* bytes);
+
+#define MCC_ADJOINT_RECOMPUTE 0
+#define MCC_ADJOINT_RECORD 1
+#define MCC_ADJOINT_REPLAY 2
 
 /*
  * mcc_adjoint: one interaction (sa, sb) of a step, recomputed from its input state, and optionally its pathwise
@@ -141,14 +150,20 @@ int mcc_adjoint_workspace_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, 
  *   gv*             [n] device, in place: in dL/dv after, out dL/dv before (all of gv*, gw, glnL or none)
  *   gw              [n] device: dL/dw accumulated (+=)
  *   glnL            device, one double: dL/dlnL_ab accumulated (+=, atomically over cells)
- *   ws, ws_bytes    at least mcc_adjoint_workspace_size bytes
- * The recomputed forward equals mcc_scatter followed by mcc_correct for the same inputs (energy passes run in order).
- * Tape overflow latches MCC_ERR_TOO_LARGE.
+ *   tape            MCC_ADJOINT_RECOMPUTE: the call runs the forward (and the reverse sweep if asked) in working
+ *                   slabs of ws, nothing kept. MCC_ADJOINT_RECORD: the same, and ws (mcc_adjoint_tape_size bytes)
+ *                   keeps every cell's tape afterwards. MCC_ADJOINT_REPLAY: the reverse sweep alone, from the tape a
+ *                   recording call on this interaction left in ws (same state, weights, lnL and parameters; the
+ *                   caller keeps them unchanged in between); P's velocities are not read, v*_out must be NULL.
+ *   ws, ws_bytes    at least mcc_adjoint_workspace_size bytes (recompute) or mcc_adjoint_tape_size bytes (record,
+ *                   replay)
+ * The recomputed forward equals mcc_scatter followed by mcc_correct for the same inputs (energy passes run in order);
+ * a replayed reverse sweep equals the recomputing one bit for bit. Tape overflow latches MCC_ERR_TOO_LARGE.
  */
 int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells, int32_t n_species,
                 const mcc_species* sp, const double* lnL, int32_t sa, int32_t sb, int32_t inter, const mcc_params* p,
                 int32_t max_cell, double* vx_out, double* vy_out, double* vz_out, double* gvx, double* gvy,
-                double* gvz, double* gw, double* glnL, void* ws, size_t ws_bytes, mcc_stream stream);
+                double* gvz, double* gw, double* glnL, int32_t tape, void* ws, size_t ws_bytes, mcc_stream stream);
 
 /* Bytes of device workspace mcc_bin needs for n particles and n_keys = n_cells * n_species segments. */
 int mcc_bin_workspace_size(int64_t n, int32_t n_cells, int32_t n_species, size_t* bytes);

@@ -118,9 +118,10 @@ def lib():
         "mcc_bin_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_bin": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t, vp]),
         "mcc_adjoint_workspace_size": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, P(C.c_size_t)]),
+        "mcc_adjoint_tape_size": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_adjoint": (C.c_int, [vp, P(_Particles), vp, C.c_int32, C.c_int32, P(_Species), P(C.c_double), C.c_int32,
-                                  C.c_int32, C.c_int32, P(_Params), C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
-                                  C.c_size_t, vp]),
+                                  C.c_int32, C.c_int32, P(_Params), C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                  C.c_int32, vp, C.c_size_t, vp]),
         "mcc_bin_weighted_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, P(C.c_size_t)]),
         "mcc_bin_weighted": (C.c_int, [vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t,
                                        vp]),
@@ -413,17 +414,36 @@ def mcc_scatter(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, sa, sb
     return backup[:, : vx.numel()]
 
 
+ADJOINT_RECOMPUTE, ADJOINT_RECORD, ADJOINT_REPLAY = 0, 1, 2
+
+
+def adjoint_tape_bytes(device, n_cells: int, max_cell: int, max_corr_passes: int) -> int:
+    """Bytes of one recorded adjoint tape (one interaction, every cell)."""
+    nb = C.c_size_t()
+    _check(lib().mcc_adjoint_tape_size(context(device).handle, int(n_cells), int(max_cell), int(max_corr_passes),
+                                       C.byref(nb)), "mcc_adjoint_tape_size")
+    return nb.value
+
+
 def mcc_adjoint(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, sa, sb, inter, params: Params,
-                max_cell: int, out=None, grad=None, gw=None, glnL=None, stream=None):
+                max_cell: int, out=None, grad=None, gw=None, glnL=None, tape: int = ADJOINT_RECOMPUTE,
+                tape_buffer=None, stream=None):
     """One interaction from the state (vx, vy, vz) before it: writes the state after it into ``out`` (three tensors)
     and/or maps ``grad`` (three tensors, dL/dv after, in place) to dL/dv before, adding dL/dw into ``gw`` and
-    dL/dlnL_ab into ``glnL`` (one-element float64 tensor). FP64, non-relativistic."""
+    dL/dlnL_ab into ``glnL`` (one-element float64 tensor). FP64, non-relativistic. With tape = ADJOINT_RECORD the
+    call keeps the interaction's tape in ``tape_buffer`` (a uint8 device tensor of adjoint_tape_bytes); a later call
+    with tape = ADJOINT_REPLAY on the same interaction runs only the reverse sweep from it."""
     ctx = context(vx.device)
     P = _particles(vx, vy, vz, w)
-    nb = C.c_size_t()
-    _check(lib().mcc_adjoint_workspace_size(ctx.handle, int(n_cells), int(max_cell), int(params.max_corr_passes),
-                                            C.byref(nb)), "mcc_adjoint_workspace_size")
-    ws = ctx.workspace("adjoint", nb.value)
+    if tape == ADJOINT_RECOMPUTE:
+        nb = C.c_size_t()
+        _check(lib().mcc_adjoint_workspace_size(ctx.handle, int(n_cells), int(max_cell), int(params.max_corr_passes),
+                                                C.byref(nb)), "mcc_adjoint_workspace_size")
+        ws, nbytes = ctx.workspace("adjoint", nb.value), nb.value
+    else:
+        if tape_buffer is None or tape_buffer.dtype != torch.uint8 or tape_buffer.device != vx.device:
+            raise TypeError("a recorded tape lives in a uint8 tensor on the particles' device")
+        ws, nbytes = tape_buffer, tape_buffer.numel()
     o = out if out is not None else (None, None, None)
     g = grad if grad is not None else (None, None, None)
     for t in [*(x for x in o if x is not None), *(x for x in g if x is not None), gw, glnL]:
@@ -432,8 +452,8 @@ def mcc_adjoint(vx, vy, vz, w, offsets, n_cells, n_species, species, lnL, sa, sb
     cp = params._c()
     _check(lib().mcc_adjoint(ctx.handle, C.byref(P), _ptr(offsets), n_cells, n_species, _species(species),
                              _lnL(lnL, n_species), sa, sb, inter, C.byref(cp), int(max_cell), _ptr(o[0]), _ptr(o[1]),
-                             _ptr(o[2]), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(gw), _ptr(glnL), _ptr(ws), nb.value,
-                             _stream(stream, vx.device)), "mcc_adjoint")
+                             _ptr(o[2]), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(gw), _ptr(glnL), int(tape),
+                             _ptr(ws), nbytes, _stream(stream, vx.device)), "mcc_adjoint")
 
 
 def mcc_correct(vx, vy, vz, w, offsets, n_cells, n_species, species, sa, sb, inter, params: Params,

@@ -743,10 +743,20 @@ int mcc_adjoint_workspace_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, 
     return MCC_OK;
 }
 
+int mcc_adjoint_tape_size(mcc_ctx* ctx, int32_t n_cells, int32_t max_cell, int32_t max_corr_passes, size_t* bytes)
+{
+    if (!ctx || !bytes || n_cells < 0 || max_cell < 0 || max_corr_passes < 0) return MCC_ERR_INVALID_ARG;
+    if (max_cell > MCC_MAX_SEGMENT) return MCC_ERR_TOO_LARGE;
+    const int32_t mc = max_cell > 0 ? max_cell : 1;
+    const int32_t ep = max_corr_passes * (mc / 2 + 1) + 1;
+    *bytes = mcc::adjoint_slab_bytes(mc, ep) * (size_t)(n_cells > 0 ? n_cells : 1);
+    return MCC_OK;
+}
+
 int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, int32_t n_cells, int32_t n_species,
                 const mcc_species* sp, const double* lnL, int32_t sa, int32_t sb, int32_t inter, const mcc_params* p,
                 int32_t max_cell, double* vx_out, double* vy_out, double* vz_out, double* gvx, double* gvy,
-                double* gvz, double* gw, double* glnL, void* ws, size_t ws_bytes, mcc_stream stream)
+                double* gvz, double* gw, double* glnL, int32_t tape, void* ws, size_t ws_bytes, mcc_stream stream)
 {
     NvtxRange nvtx_("mcc_adjoint");
     if (!ctx || !P || !offsets || !sp || !lnL || !valid_params(p) || inter < 0 || inter > 0xFFFFFF || max_cell < 0)
@@ -756,6 +766,8 @@ int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
     const bool fwd = vx_out || vy_out || vz_out, rev = gvx || gvy || gvz;
     if (fwd && !(vx_out && vy_out && vz_out)) return MCC_ERR_INVALID_ARG;
     if (rev && !(gvx && gvy && gvz && gw && glnL)) return MCC_ERR_INVALID_ARG;
+    if (tape < MCC_ADJOINT_RECOMPUTE || tape > MCC_ADJOINT_REPLAY || (tape == MCC_ADJOINT_REPLAY && fwd))
+        return MCC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     StepArgs a;
     const int32_t ab[2] = {sa, sb};
@@ -763,12 +775,13 @@ int mcc_adjoint(mcc_ctx* ctx, const mcc_particles* P, const int64_t* offsets, in
     if (rc != MCC_OK) return rc;
     if (n_cells == 0 || (!fwd && !rev)) return MCC_OK;
     size_t need = 0;
-    mcc_adjoint_workspace_size(ctx, n_cells, max_cell, p->max_corr_passes, &need);
+    if (tape == MCC_ADJOINT_RECOMPUTE) mcc_adjoint_workspace_size(ctx, n_cells, max_cell, p->max_corr_passes, &need);
+    else mcc_adjoint_tape_size(ctx, n_cells, max_cell, p->max_corr_passes, &need);
     if (!ws || ws_bytes < need) return MCC_ERR_WORKSPACE;
     const int32_t mc = max_cell > 0 ? max_cell : 1;
     const int32_t ep = p->max_corr_passes * (mc / 2 + 1) + 1;
     const cudaError_t e = mcc::launch_adjoint(a, lnL[sa * n_species + sb], vx_out, vy_out, vz_out, gvx, gvy, gvz, gw,
-                                              glnL, reinterpret_cast<char*>(ws), mc, ep,
+                                              glnL, reinterpret_cast<char*>(ws), mc, ep, tape,
                                               adjoint_grid(ctx, n_cells), S(stream));
     ctx->launches += 1;
     return cuda_status(e);

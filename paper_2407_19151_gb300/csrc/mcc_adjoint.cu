@@ -17,7 +17,9 @@
 // the first pair of the order as the crossing pair with U = Delta E_s = 0.
 // The kernel recomputes the interaction from the stored pre-interaction state, keeping a tape of every pair's inputs,
 // then runs the chain rule backwards through the tape (one CTA per cell, the cell's working arrays in a per-CTA slab
-// of the workspace).
+// of the workspace). With a recorded tape the slabs are per cell and outlive the call: a recording call runs the
+// forward and keeps each cell's slab (the tape and the per-cell scalars of the correction); a later replaying call on
+// the same interaction runs only the reverse sweep from it.
 #include "mcc_kernels.h"
 
 namespace mcc {
@@ -40,6 +42,13 @@ struct AdjArgs {
     int64_t slab_stride;
     int32_t max_cell;
     int32_t max_epairs;
+    int32_t tape;              // 0: per-CTA slabs, recompute; 1: per-cell slabs, record; 2: per-cell slabs, replay
+};
+
+// Per-cell scalars of the forward that the reverse sweep reads (kept at the end of a recorded slab).
+struct TapeHead {
+    int fail, ne[2], e0[2], zeroed[2];
+    double B[3], Sw, S[3], dE, Es[2], W1[2], D[2];
 };
 
 // Per-CTA working arrays (n = max_cell, E = max_epairs).
@@ -64,6 +73,7 @@ struct Slab {
     int32_t* ei;    // [E] energy pair particles, capped flag
     int32_t* ej;
     int32_t* ecap;
+    TapeHead* head;
     int n, E;
 };
 
@@ -73,7 +83,7 @@ __host__ __device__ inline size_t slab_bytes(int n, int E)
 {
     const size_t dn = (size_t)n, de = (size_t)E;
     return al8(8 * dn) + 6 * al8(24 * dn) + al8(8 * dn) + al8(48 * dn) + al8(48 * de) + 2 * al8(8 * de) +
-           5 * al8(4 * dn) + 3 * al8(4 * de) + 256;
+           5 * al8(4 * dn) + 3 * al8(4 * de) + al8(sizeof(TapeHead)) + 256;
 }
 
 __device__ Slab make_slab(char* base, int n, int E)
@@ -107,6 +117,7 @@ __device__ Slab make_slab(char* base, int n, int E)
     s.ei = reinterpret_cast<int32_t*>(take(4 * (size_t)E));
     s.ej = reinterpret_cast<int32_t*>(take(4 * (size_t)E));
     s.ecap = reinterpret_cast<int32_t*>(take(4 * (size_t)E));
+    s.head = reinterpret_cast<TapeHead*>(take(sizeof(TapeHead)));
     return s;
 }
 
@@ -325,9 +336,10 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ Ad
     const double* gvx = reinterpret_cast<const double*>(A.vx);
     const double* gvy = reinterpret_cast<const double*>(A.vy);
     const double* gvz = reinterpret_cast<const double*>(A.vz);
-    Slab sl = make_slab(G.slab + (size_t)blockIdx.x * (size_t)G.slab_stride, G.max_cell, G.max_epairs);
     const uint32_t ictr = (uint32_t)A.inter_base;
     for (int c = blockIdx.x; c < A.n_cells; c += gridDim.x) {
+        const Slab sl = make_slab(G.slab + (size_t)(G.tape ? c : (int)blockIdx.x) * (size_t)G.slab_stride, G.max_cell,
+                                  G.max_epairs);
         const int64_t cs = A.offsets[(int64_t)c * S];
         const int n = (int)(A.offsets[(int64_t)(c + 1) * S] - cs);
         const int N = sl.n;
@@ -337,9 +349,11 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ Ad
         }
         if ((int)threadIdx.x <= S) sh.off[threadIdx.x] = (int)(A.offsets[(int64_t)c * S + threadIdx.x] - cs);
         for (int i = threadIdx.x; i < n; i += kThreads) {
-            const double x[3] = {gvx[cs + i], gvy[cs + i], gvz[cs + i]};
-            st3(sl.v, N, i, x);
-            st3(sl.vb, N, i, x);
+            if (G.tape != 2) {  // a replaying call finds the state before the interaction in the tape
+                const double x[3] = {gvx[cs + i], gvy[cs + i], gvz[cs + i]};
+                st3(sl.v, N, i, x);
+                st3(sl.vb, N, i, x);
+            }
             sl.gwl[i] = 0.0;
         }
         __syncthreads();
@@ -347,7 +361,28 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ Ad
         const int b0 = sh.off[ic.b], nb = sh.off[ic.b + 1] - b0;
         const bool active = intra ? (na >= 2) : (na > 0 && nb > 0);
         const int nside = intra ? 1 : 2;
-        if (active) {
+        if (active && G.tape == 2) {
+            // ---- replay: the forward's per-cell scalars from the tape
+            if (threadIdx.x == 0) {
+                const TapeHead& h = *sl.head;
+                sh.fail = h.fail;
+                for (int k = 0; k < 2; ++k) {
+                    sh.ne[k] = h.ne[k];
+                    sh.e0[k] = h.e0[k];
+                    sh.zeroed[k] = h.zeroed[k];
+                    sh.Es[k] = h.Es[k];
+                    sh.W1[k] = h.W1[k];
+                    sh.D[k] = h.D[k];
+                }
+                for (int k = 0; k < 3; ++k) {
+                    sh.B[k] = h.B[k];
+                    sh.S[k] = h.S[k];
+                }
+                sh.Sw = h.Sw;
+                sh.dE = h.dE;
+            }
+            __syncthreads();
+        } else if (active) {
             // ---- forward: permutations (sorted Philox keys)
             for (int side = 0; side < nside; ++side) {
                 const int s0 = side ? b0 : a0, ns = side ? nb : na;
@@ -582,6 +617,24 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ Ad
                 }
                 if (sh.fail && A.fail_policy == 2 && threadIdx.x == 0) latch(A.status, kErrCorrectionFailed);
                 __syncthreads();
+            }
+            if (G.tape == 1 && threadIdx.x == 0) {  // record: keep the per-cell scalars with the tape
+                TapeHead& h = *sl.head;
+                h.fail = A.correct ? sh.fail : 0;
+                for (int k = 0; k < 2; ++k) {
+                    h.ne[k] = sh.ne[k];
+                    h.e0[k] = sh.e0[k];
+                    h.zeroed[k] = sh.zeroed[k];
+                    h.Es[k] = sh.Es[k];
+                    h.W1[k] = sh.W1[k];
+                    h.D[k] = sh.D[k];
+                }
+                for (int k = 0; k < 3; ++k) {
+                    h.B[k] = sh.B[k];
+                    h.S[k] = sh.S[k];
+                }
+                h.Sw = sh.Sw;
+                h.dE = sh.dE;
             }
         }
         // ---- forward output
@@ -822,7 +875,7 @@ size_t adjoint_slab_bytes(int32_t max_cell, int32_t max_epairs) { return (slab_b
 
 cudaError_t launch_adjoint(const StepArgs& a, double lnL, double* ox, double* oy, double* oz, double* gx, double* gy,
                            double* gz, double* gw, double* glnL, char* slab, int32_t max_cell, int32_t max_epairs,
-                           int grid, cudaStream_t st)
+                           int32_t tape, int grid, cudaStream_t st)
 {
     AdjArgs g;
     g.a = a;
@@ -839,6 +892,7 @@ cudaError_t launch_adjoint(const StepArgs& a, double lnL, double* ox, double* oy
     g.slab_stride = (int64_t)adjoint_slab_bytes(max_cell, max_epairs);
     g.max_cell = max_cell;
     g.max_epairs = max_epairs;
+    g.tape = tape;
     k_adjoint<<<grid, kThreads, 0, st>>>(g);
     return cudaGetLastError();
 }

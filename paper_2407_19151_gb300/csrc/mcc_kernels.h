@@ -125,6 +125,7 @@ int64_t static_bin_max_keys();
 size_t adjoint_slab_bytes(int32_t max_cell, int32_t max_epairs);
 cudaError_t launch_adjoint(const StepArgs& a, double lnL, double* ox, double* oy, double* oz, double* gx, double* gy,
                            double* gz, double* gw, double* glnL, char* slab, int32_t max_cell, int32_t max_epairs,
+                           int32_t tape,
                            int grid, cudaStream_t st);
 cudaError_t launch_gather(const void* in, const int32_t* perm, int64_t n, int elem_bytes, void* out, cudaStream_t st);
 

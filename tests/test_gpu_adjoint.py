@@ -57,14 +57,14 @@ def test_adjoint_forward_matches_oracle(mcc, method):
     assert np.abs(got - ref).max() / scale < 1e-12
 
 
-def _grads(mcc, wl, kw, cot_fn, n_steps=2, every=10):
+def _grads(mcc, wl, kw, cot_fn, n_steps=2, every=10, tape=False):
     import torch
     v, w, off, L = _tensors(wl)
     for x in (*v, w, L):
         x.requires_grad_(True)
     sp = list(zip(wl.q.tolist(), wl.m.tolist()))
     out = mcc.collision_steps(*v, w, L, off, wl.n_cells, wl.n_species, sp, mcc.Params(**kw), n_steps,
-                              checkpoint_every=every)
+                              checkpoint_every=every, tape=tape)
     vf = np.stack([x.detach().cpu().numpy() for x in out], axis=1)
     cot = torch.tensor(cot_fn(vf), device="cuda")
     loss = sum((cot[:, d] * out[d]).sum() for d in range(3))
@@ -169,6 +169,39 @@ def test_adjoint_equals_oracle_autodiff(mcc, method, case):
     assert np.abs(gv - gvo).max() <= 1e-9 * np.abs(gvo).max(), np.unravel_index(np.argmax(np.abs(gv - gvo)), gv.shape)
     assert np.abs(gw - gwo).max() <= 1e-9 * np.abs(gwo).max(), int(np.argmax(np.abs(gw - gwo)))
     assert np.abs(gL - gLo).max() <= 1e-9 * np.abs(gLo).max(), (gL, gLo)
+
+
+@pytest.mark.parametrize("case", ["even", "poisson"])
+def test_adjoint_recorded_tape(mcc, case):
+    """Recorded tapes (the forward through the adjoint kernel, the backward the reverse sweep alone): the forward
+    equals the oracle step, and the gradient equals the checkpointing mode's and the reverse-mode oracle gradient
+    entry by entry."""
+    wl, kw = _case(W.N97, n_cells=8, per_species=24) if case == "even" else _poisson_case(W.N97)
+    rng = np.random.default_rng(23)
+    cot = rng.standard_normal((wl.n, 3))
+    vt, gvt, gwt, gLt = _grads(mcc, wl, kw, lambda vf: cot, n_steps=3, tape=True)
+    vc, gvc, gwc, gLc = _grads(mcc, wl, kw, lambda vf: cot, n_steps=3, every=2)
+    v0 = np.stack([wl.vx, wl.vy, wl.vz], axis=1)
+    vo, gvo, gwo, gLo = AD.gradient(cot, v0, wl.w, wl.lnL, wl.offsets, wl.n_cells, wl.n_species, wl.q, wl.m,
+                                    O.Params(**kw), 3)
+    assert np.abs(vt - vo).max() <= 1e-12 * np.abs(vo).max()
+    for a, b, c in ((gvt, gvc, gvo), (gwt, gwc, gwo), (gLt, gLc, gLo)):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(c).max()
+        assert np.abs(a - c).max() <= 1e-9 * np.abs(c).max()
+
+
+def test_adjoint_replay_without_record_rejected(mcc):
+    """A replaying call cannot also ask for the forward outputs (it runs no forward)."""
+    import torch
+    wl, kw = _case(W.N97)
+    v, w, off, _ = _tensors(wl)
+    sp = list(zip(wl.q.tolist(), wl.m.tolist()))
+    mc = int(wl.counts.sum(1).max())
+    buf = torch.empty(mcc.adjoint_tape_bytes(0, wl.n_cells, mc, 8), dtype=torch.uint8, device="cuda")
+    out = [torch.empty_like(x) for x in v]
+    with pytest.raises(mcc.MccError):
+        mcc.mcc_adjoint(*v, w, off, wl.n_cells, wl.n_species, sp, wl.lnL, 0, 0, 0, mcc.Params(**kw), mc, out=out,
+                        tape=mcc.ADJOINT_REPLAY, tape_buffer=buf)
 
 
 def test_adjoint_checkpoint_segments_agree(mcc):
