@@ -16,6 +16,7 @@ workload, and the oracle timed on the host cores on a bounded sample of cells.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -74,9 +75,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+DOMINANT_KERNEL_SOURCES = ("mcc_group.cuh", "mcc_group_f32.cu", "mcc_device.cuh", "mcc_kernels.h")
+
+
 def kernel_source_hash() -> str:
-    from paper_2407_19151_gb300._build import source_hash
-    return source_hash()
+    """Hash of the sources the mixed-path group kernels are compiled from (the committed ncu record is valid only
+    for the kernel source it was taken on)."""
+    h = hashlib.sha256()
+    for f in DOMINANT_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2407_19151_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_entry(workload: str):
@@ -92,11 +101,6 @@ def ncu_entry(workload: str):
     except Exception:
         pass
     return None
-
-
-def ncu_traffic(workload: str):
-    e = ncu_entry(workload)
-    return float(e["dram_bytes_per_launch"]) if e else None
 
 
 class ClockSampler:

@@ -2,9 +2,9 @@
 // species s, sum w, sum m w v (three components), sum of the kinetic energy (1/2 m w |v|^2, or m w c^2 (gamma - 1)
 // for proper velocities) and the particle count, plus the sum of the per-cell failure counts.
 //
-// One CTA per group of cells (grid-stride): each thread accumulates its particles' contributions per species in
-// registers (FP64), the CTA reduces them in shared memory and adds its partial sums to the output with double
-// atomics, so the summation order varies between runs at the rounding level.
+// One CTA per group of cells (grid-stride), one species at a time: each thread accumulates its particles'
+// contributions in six FP64 registers, the CTA reduces them with warp shuffles and shared memory and adds its partial
+// sums to the output with double atomics, so the summation order varies between runs at the rounding level.
 #include "mcc_kernels.h"
 
 namespace mcc {
@@ -21,37 +21,27 @@ __global__ void __launch_bounds__(kMomThreads) k_species_moments(const V* __rest
                                                                  const int32_t* __restrict__ fail_count, double* out)
 {
     __shared__ double red[kMomThreads / 32][kMomFields];
-    double acc[kMaxSpecies][kMomFields];
-#pragma unroll
-    for (int s = 0; s < kMaxSpecies; ++s)
-#pragma unroll
-        for (int f = 0; f < kMomFields; ++f) acc[s][f] = 0.0;
-    double fails = 0.0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const double c2 = c * c;
-    for (int32_t cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
-#pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) {
-            if (s >= S) break;
+    for (int s = 0; s < S; ++s) {
+        const double m = sc.m[s];
+        double acc[kMomFields] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int32_t cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
             const int64_t b = offsets[(int64_t)cell * S + s], e = offsets[(int64_t)cell * S + s + 1];
-            const double m = sc.m[s];
             for (int64_t i = b + threadIdx.x; i < e; i += kMomThreads) {
                 const double x = (double)vx[i], y = (double)vy[i], z = (double)vz[i], mw = m * w[i];
                 const double v2 = x * x + y * y + z * z;
-                acc[s][0] += w[i];
-                acc[s][1] += mw * x;
-                acc[s][2] += mw * y;
-                acc[s][3] += mw * z;
-                acc[s][4] += rel ? mw * v2 / (sqrt(1.0 + v2 / c2) + 1.0) : 0.5 * mw * v2;
-                acc[s][5] += 1.0;
+                acc[0] += w[i];
+                acc[1] += mw * x;
+                acc[2] += mw * y;
+                acc[3] += mw * z;
+                acc[4] += rel ? mw * v2 / (sqrt(1.0 + v2 / c2) + 1.0) : 0.5 * mw * v2;
+                acc[5] += 1.0;
             }
         }
-        if (fail_count && threadIdx.x == 0) fails += (double)fail_count[cell];
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int s = 0; s < S; ++s) {
 #pragma unroll
         for (int f = 0; f < kMomFields; ++f) {
-            double x = acc[s][f];
+            double x = acc[f];
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             if (lane == 0) red[wid][f] = x;
         }
@@ -63,7 +53,13 @@ __global__ void __launch_bounds__(kMomThreads) k_species_moments(const V* __rest
         }
         __syncthreads();
     }
-    if (fail_count && threadIdx.x == 0 && fails != 0.0) atomicAdd(&out[S * kMomFields], fails);
+    if (fail_count) {
+        double f = 0.0;
+        for (int32_t cell = blockIdx.x * kMomThreads + threadIdx.x; cell < n_cells; cell += gridDim.x * kMomThreads)
+            f += (double)fail_count[cell];
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0 && f != 0.0) atomicAdd(&out[S * kMomFields], f);
+    }
 }
 
 }  // namespace
