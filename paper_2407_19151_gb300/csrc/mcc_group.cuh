@@ -39,6 +39,7 @@
 namespace mcc {
 namespace grp {
 
+
 // Bounds-checked build (-DMCC_DEBUG_BOUNDS): every tile and global index of the group kernels is checked against
 // the bound of what it indexes; the first violation latches kErrBounds in the status word and records (source line,
 // index, bound, count) in rec[0..3]; the access then uses index 0 instead (results are garbage, memory is safe).
@@ -1162,6 +1163,26 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
     return neg ? ff_neg(absorbed) : absorbed;
 }
 
+// The 64- and 128-thread groups call one out-of-line copy of the energy loop from every call site (and of the cell
+// load, below): 2-4% faster there on the three-species workload, slower for the other group sizes.
+template <int G>
+constexpr bool kOutline = G == 64 || G == 128;
+
+template <bool REL, int WIDTH>
+__device__ __noinline__ ff energy_loop_ool(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc,
+                                           int mode, ff D, int& used, bool& done)
+{
+    return energy_loop<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
+}
+
+template <bool REL, int WIDTH, int G>
+__device__ __forceinline__ ff energy_call(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc,
+                                          int mode, ff D, int& used, bool& done)
+{
+    if constexpr (kOutline<G>) return energy_loop_ool<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
+    else return energy_loop<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
+}
+
 // Moment correction of one interaction (Sec. 4, Appendix A, Sec. 5.2). Returns 1 if the interaction failed under
 // the rollback policy (the caller replays the cell without it).
 template <bool REL, int G>
@@ -1306,8 +1327,8 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
                 const int s0 = side ? b0 : a0, ns = side ? nb : na, spc = side ? ic.b : ic.a;
                 const int mode = A.sort_by_weight ? sh.wmode[spc] : 1;
                 int u = 0;
-                const ff ab = G == 32 ? energy_loop<REL, 16>(A, t, cs, s0, ns, spc, mode, Ds, u, done)
-                                      : energy_loop<REL, 32>(A, t, cs, s0, ns, spc, mode, Ds, u, done);
+                const ff ab = G == 32 ? energy_call<REL, 16, G>(A, t, cs, s0, ns, spc, mode, Ds, u, done)
+                                      : energy_call<REL, 32, G>(A, t, cs, s0, ns, spc, mode, Ds, u, done);
                 if (side) {
                     Eaft1 = ff_sub(Eaft1, ab);
                     used1 = u;
@@ -1323,13 +1344,13 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
             if (!fail && !ff_is0(D0)) {
                 bool done;
                 const int mode = A.sort_by_weight ? sh.wmode[ic.a] : 1;
-                Eaft0 = ff_sub(Eaft0, energy_loop<REL, 32>(A, t, cs, a0, na, ic.a, mode, D0, used0, done));
+                Eaft0 = ff_sub(Eaft0, energy_call<REL, 32, G>(A, t, cs, a0, na, ic.a, mode, D0, used0, done));
                 if (!done) fail0 = 1;
             }
             if (!fail && !fail0 && !intra && !ff_is0(D1)) {
                 bool done;
                 const int mode = A.sort_by_weight ? sh.wmode[ic.b] : 1;
-                Eaft1 = ff_sub(Eaft1, energy_loop<REL, 32>(A, t, cs, b0, nb, ic.b, mode, D1, used1, done));
+                Eaft1 = ff_sub(Eaft1, energy_call<REL, 32, G>(A, t, cs, b0, nb, ic.b, mode, D1, used1, done));
                 if (!done) fail1 = 1;
             }
         }
@@ -1442,6 +1463,19 @@ __device__ void gload(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t
 }
 
 template <bool REL, int G>
+__device__ __noinline__ void gload_ool(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t cs, int S)
+{
+    gload<REL, G>(A, t, sh, cs, S);
+}
+
+template <bool REL, int G>
+__device__ __forceinline__ void gload_call(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t cs, int S)
+{
+    if constexpr (kOutline<G>) gload_ool<REL, G>(A, t, sh, cs, S);
+    else gload<REL, G>(A, t, sh, cs, S);
+}
+
+template <bool REL, int G>
 __device__ void gcell(const StepArgs& A, int c, unsigned char* dyn, GShared<G>& sh)
 {
     const int S = A.S;
@@ -1465,7 +1499,7 @@ __device__ void gcell(const StepArgs& A, int c, unsigned char* dyn, GShared<G>& 
     for (int q = 0; q < 8; ++q) pc.acc[q] = 0;
 #endif
     const uint32_t step = sh.step;
-    gload<REL, G>(A, t, sh, cs, S);
+    gload_call<REL, G>(A, t, sh, cs, S);
     PHASE_MARK(pc, 0);
     uint64_t skip = 0;
     for (int k = 0; k < A.n_inter; ++k) {
@@ -1485,7 +1519,7 @@ __device__ void gcell(const StepArgs& A, int c, unsigned char* dyn, GShared<G>& 
         if (gcorrect<REL, G>(A, t, sh, c, cs, k, ic, intra, a0, na, b0, nb, pc)) {
             // Sec. 5.2 fallback: the cell restarts from its stored state without the failed interaction
             skip |= 1ull << k;
-            gload<REL, G>(A, t, sh, cs, S);
+            gload_call<REL, G>(A, t, sh, cs, S);
             PHASE_MARK(pc, 0);
             k = -1;
         }
