@@ -290,48 +290,6 @@ __device__ __forceinline__ int block_sum_int(int x, int* scratch)
     return s;
 }
 
-__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m)
-{
-    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
-    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
-    return ((uint64_t)hi << 32) | lo;
-}
-
-// Bitonic sort (ascending) of 32*K 64-bit keys held in registers by one warp, K per lane: lane l holds positions
-// l*K .. l*K + K - 1. Strides below K stay in the lane's registers, larger ones exchange with lane ^ (stride / K).
-template <int K>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&x)[K])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int size = 2; size <= 32 * K; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= K) {
-#pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    const int pos = lane * K + r;
-                    const uint64_t y = shfl_xor_u64(x[r], stride / K);
-                    const bool keep_min = ((pos & size) == 0) == ((pos & stride) == 0);
-                    x[r] = keep_min ? (x[r] < y ? x[r] : y) : (x[r] < y ? y : x[r]);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    if ((r & stride) == 0) {
-                        const int pos = lane * K + r;
-                        const uint64_t a = x[r], b = x[r + stride];
-                        const bool up = (pos & size) == 0;
-                        const bool swap = up ? (a > b) : (a < b);
-                        x[r] = swap ? b : a;
-                        x[r + stride] = swap ? a : b;
-                    }
-                }
-            }
-        }
-    }
-}
-
 // Ascending sort of n 64-bit keys in place (shared or global memory), block-wide. Bitonic network in its "flip"
 // form: every comparator puts the minimum at the lower index, so positions >= n act as +infinity and are skipped.
 __device__ __forceinline__ void cmpx(uint64_t* a, int lo, int hi)
@@ -404,36 +362,45 @@ __device__ __forceinline__ void block_sort_i32(int32_t* a, int n)
     }
 }
 
-constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp in registers
+constexpr int kWarpSortMax = 512;  // segments up to this size are sorted by one warp
 
-// Ascending sort of n <= 512 keys in buf (shared or global) by the calling warp: loaded K per lane into registers,
-// bitonic network, stored back. One out-of-line copy per K keeps register pressure and code size off the callers.
-template <int K>
-__device__ __noinline__ void warp_sort_buf_k(uint64_t* buf, int n)
+// Ascending sort of n <= 512 keys in place in buf (shared or global) by the calling warp: the bitonic network in
+// its "flip" form (positions >= n act as +infinity), one warp barrier per stage. The loops stay rolled: fully
+// unrolled register networks (one per size up to 512) took over half of each step kernel's code, and the step ran
+// 17% slower on unordered segments through instruction-cache misses.
+static __device__ __noinline__ void warp_sort_rolled(uint64_t* a, int n)
 {
     const int lane = threadIdx.x & 31;
-    uint64_t x[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        x[r] = pos < n ? buf[pos] : ~0ull;
-    }
-    warp_bitonic<K>(x);
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const int pos = lane * K + r;
-        if (pos < n) buf[pos] = x[r];
+    int logP = 0;
+    while ((1 << logP) < n) ++logP;
+    const int half_work = 1 << (logP - 1);
+#pragma unroll 1
+    for (int lg = 1; lg <= logP; ++lg) {
+        const int size = 1 << lg, hmask = (size >> 1) - 1;
+#pragma unroll 1
+        for (int i = lane; i < half_work; i += 32) {
+            const int base = (i >> (lg - 1)) << lg;
+            const int lo = base + (i & hmask), hi = base + size - 1 - (i & hmask);
+            if (hi < n) cmpx(a, lo, hi);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int ls = lg - 2; ls >= 0; --ls) {
+            const int stride = 1 << ls;
+#pragma unroll 1
+            for (int i = lane; i < half_work; i += 32) {
+                const int lo = ((i >> ls) << (ls + 1)) + (i & (stride - 1)), hi = lo + stride;
+                if (hi < n) cmpx(a, lo, hi);
+            }
+            __syncwarp();
+        }
     }
 }
 
 __device__ __forceinline__ void warp_sort_buf(uint64_t* buf, int n)
 {
     __syncwarp();
-    if (n <= 32) warp_sort_buf_k<1>(buf, n);
-    else if (n <= 64) warp_sort_buf_k<2>(buf, n);
-    else if (n <= 128) warp_sort_buf_k<4>(buf, n);
-    else if (n <= 256) warp_sort_buf_k<8>(buf, n);
-    else warp_sort_buf_k<16>(buf, n);
+    if (n >= 2) warp_sort_rolled(buf, n);
     __syncwarp();
 }
 

@@ -723,8 +723,9 @@ __device__ __forceinline__ float pair_kecm_ff(float cc, ff c2inv, float m1, floa
 // lowered by U, alpha the root of smaller magnitude of a alpha^2 + b alpha + c0 = 0 (the coefficients of
 // energy_pair<., true>, cancellation-free forms). Masses and U are taken in units of m1 + m2 (the quadratic is
 // homogeneous of degree one in them: alpha scales with the masses), which keeps b^2 and c0 inside float's range.
-// Updates u1, u2 (float-float) in place.
-__device__ __forceinline__ void energy_pair_rel_ff(ff c2inv, ff m1, ff m2, ff u1[3], ff u2[3], ff U)
+// Updates u1, u2 (float-float) in place. Out of line: it runs once per species and interaction (the crossing pair)
+// and its code is large.
+static __device__ __noinline__ void energy_pair_rel_ff(ff c2inv, ff m1, ff m2, ff u1[3], ff u2[3], ff U)
 {
     const ff M12 = ff_add(m1, m2);
     const ff n1 = ffq_div(m1, M12), n2 = ffq_div(m2, M12);
@@ -1163,10 +1164,12 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
     return neg ? ff_neg(absorbed) : absorbed;
 }
 
-// The 64- and 128-thread groups call one out-of-line copy of the energy loop from every call site (and of the cell
-// load, below): 2-4% faster there on the three-species workload, slower for the other group sizes.
-template <int G>
-constexpr bool kOutline = G == 64 || G == 128;
+// The 64- and 128-thread groups and every relativistic group call one out-of-line copy of the energy loop from every
+// call site (and of the cell load, below): 2-4% faster there (a smaller instruction footprint), slower for the other
+// non-relativistic group sizes.
+template <bool REL, int G>
+constexpr bool kOutline = REL || G == 64 || G == 128;
+
 
 template <bool REL, int WIDTH>
 __device__ __noinline__ ff energy_loop_ool(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc,
@@ -1179,7 +1182,7 @@ template <bool REL, int WIDTH, int G>
 __device__ __forceinline__ ff energy_call(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc,
                                           int mode, ff D, int& used, bool& done)
 {
-    if constexpr (kOutline<G>) return energy_loop_ool<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
+    if constexpr (kOutline<REL, G>) return energy_loop_ool<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
     else return energy_loop<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
 }
 
@@ -1471,7 +1474,7 @@ __device__ __noinline__ void gload_ool(const StepArgs& A, const GTile& t, GShare
 template <bool REL, int G>
 __device__ __forceinline__ void gload_call(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t cs, int S)
 {
-    if constexpr (kOutline<G>) gload_ool<REL, G>(A, t, sh, cs, S);
+    if constexpr (kOutline<REL, G>) gload_ool<REL, G>(A, t, sh, cs, S);
     else gload<REL, G>(A, t, sh, cs, S);
 }
 
