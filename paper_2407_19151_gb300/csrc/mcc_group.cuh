@@ -264,21 +264,25 @@ __device__ __forceinline__ void greduce_warp0(ff (&a)[P], GRed<G, 8>& r)
     }
 }
 
-// Exclusive prefix sum of one value per lane in lane order over a segment of WIDTH (16 or 32) lanes of the warp
-// (lanes given by mask), and the segment total.
+// Exclusive prefix sum of one value per lane in lane order over a segment of W (16 or 32) lanes of the warp (lanes
+// given by mask), and the segment total. W = WIDTH, or the runtime width when WIDTH is 0 (one copy of the code serves
+// both segment widths).
 template <int WIDTH>
-__device__ __forceinline__ ff seg_scan_excl(ff x, unsigned mask, ff& total)
+__device__ __forceinline__ ff seg_scan_excl(ff x, unsigned mask, int width, ff& total)
 {
-    const int lane = threadIdx.x & (WIDTH - 1);
+    const int W = WIDTH ? WIDTH : width;
+    const int lane = threadIdx.x & (W - 1);
     ff inc = x;
 #pragma unroll
-    for (int o = 1; o < WIDTH; o <<= 1) {
-        const ff y = {__shfl_up_sync(mask, inc.hi, o, WIDTH), __shfl_up_sync(mask, inc.lo, o, WIDTH)};
-        if (lane >= o) inc = ff_add(y, inc);
+    for (int o = 1; o < 32; o <<= 1) {
+        if (o < W) {
+            const ff y = {__shfl_up_sync(mask, inc.hi, o, W), __shfl_up_sync(mask, inc.lo, o, W)};
+            if (lane >= o) inc = ff_add(y, inc);
+        }
     }
-    ff exc = {__shfl_up_sync(mask, inc.hi, 1, WIDTH), __shfl_up_sync(mask, inc.lo, 1, WIDTH)};
+    ff exc = {__shfl_up_sync(mask, inc.hi, 1, W), __shfl_up_sync(mask, inc.lo, 1, W)};
     if (lane == 0) exc = {0.f, 0.f};
-    total = {__shfl_sync(mask, inc.hi, WIDTH - 1, WIDTH), __shfl_sync(mask, inc.lo, WIDTH - 1, WIDTH)};
+    total = {__shfl_sync(mask, inc.hi, W - 1, W), __shfl_sync(mask, inc.lo, W - 1, W)};
     return exc;
 }
 
@@ -1052,8 +1056,9 @@ __device__ __forceinline__ ff ke_per_mass(const ff v[3], ff c2inv)
 }
 
 // ----------------------------------------------------------------------------------------------- correction
-// Energy-correction loop of one species (Algorithm 1, final loop) by a segment of WIDTH lanes (a warp, or a half
-// warp): pairs of adjacent particles of the order rho, pass p from offset p mod 2, in chunks of WIDTH pairs; each pair takes U = fE KE_cm (its cap) up to
+// Energy-correction loop of one species (Algorithm 1, final loop) by a segment of W lanes (a warp, or a half warp;
+// W = WIDTH, or the runtime width when WIDTH is 0): pairs of adjacent particles of the order rho, pass p from offset
+// p mod 2, in chunks of W pairs; each pair takes U = fE KE_cm (its cap) up to
 // the crossing pair, which takes the remainder of |Delta E_s| (a prefix sum over the caps gives every pair the sum
 // of the caps before it). Non-relativistic pairs in float-float (Eqs. vp1_inelastic, vp2_inelastic, vrel_inelastic:
 // a capped pair has U / KE_cm = +-fE, so its g - 1 is a constant); relativistic pairs through the Appendix A
@@ -1061,10 +1066,11 @@ __device__ __forceinline__ ff ke_per_mass(const ff v[3], ff c2inv)
 // absorbed.
 template <bool REL, int WIDTH>
 __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc, int mode, ff D,
-                          int& used, bool& done)
+                          int width, int& used, bool& done)
 {
-    const int lane = threadIdx.x & (WIDTH - 1);
-    const unsigned mask = WIDTH == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    const int W = WIDTH ? WIDTH : width;
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned mask = W == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
     const int cap = t.cap;
     const ff ms = mass_ff(A, spc);
     const ff fE = {A.fE_f, A.fE_lo};
@@ -1079,7 +1085,7 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
         const int o = pass & 1;
         const int np = (ns - o) / 2;
         ff carry = {0.f, 0.f};
-        for (int base = 0; base < np && !done; base += WIDTH) {
+        for (int base = 0; base < np && !done; base += W) {
             const int m = base + lane;
             const bool valid = m < np;
             int i = 0, j = 0;
@@ -1122,7 +1128,7 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
                 if (!(K.hi > 0.f)) capx = {0.f, 0.f};
             }
             ff total;
-            const ff excl = ff_add(seg_scan_excl<WIDTH>(capx, mask, total), carry);
+            const ff excl = ff_add(seg_scan_excl<WIDTH>(capx, mask, W, total), carry);
             if (valid && K.hi > 0.f && ff_lt(excl, Dabs)) {
                 const ff rem = ff_sub(Dabs, excl);
                 const bool crossing = ff_lt(rem, capx);
@@ -1164,26 +1170,26 @@ __device__ ff energy_loop(const StepArgs& A, const GTile& t, int64_t cs, int s0,
     return neg ? ff_neg(absorbed) : absorbed;
 }
 
-// The 64- and 128-thread groups and every relativistic group call one out-of-line copy of the energy loop from every
-// call site (and of the cell load, below): 2-4% faster there (a smaller instruction footprint), slower for the other
-// non-relativistic group sizes.
+// Out-of-line copies (smaller instruction footprint of the cell visit): the energy loop for every group; the cell load
+// for the 64- and 128-thread groups and every relativistic group (2-4% faster there, slower for the other
+// non-relativistic group sizes).
 template <bool REL, int G>
 constexpr bool kOutline = REL || G == 64 || G == 128;
 
-
 template <bool REL, int WIDTH>
 __device__ __noinline__ ff energy_loop_ool(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc,
-                                           int mode, ff D, int& used, bool& done)
+                                           int mode, ff D, int width, int& used, bool& done)
 {
-    return energy_loop<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
+    return energy_loop<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, width, used, done);
 }
 
-template <bool REL, int WIDTH, int G>
+// One out-of-line copy of the energy loop serves every call site; one-warp groups run it on a whole warp or on half
+// warps, with the width at run time.
+template <bool REL, int G>
 __device__ __forceinline__ ff energy_call(const StepArgs& A, const GTile& t, int64_t cs, int s0, int ns, int spc,
-                                          int mode, ff D, int& used, bool& done)
+                                          int mode, ff D, int width, int& used, bool& done)
 {
-    if constexpr (kOutline<REL, G>) return energy_loop_ool<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
-    else return energy_loop<REL, WIDTH>(A, t, cs, s0, ns, spc, mode, D, used, done);
+    return energy_loop_ool<REL, G == 32 ? 0 : 32>(A, t, cs, s0, ns, spc, mode, D, width, used, done);
 }
 
 // Moment correction of one interaction (Sec. 4, Appendix A, Sec. 5.2). Returns 1 if the interaction failed under
@@ -1330,8 +1336,7 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
                 const int s0 = side ? b0 : a0, ns = side ? nb : na, spc = side ? ic.b : ic.a;
                 const int mode = A.sort_by_weight ? sh.wmode[spc] : 1;
                 int u = 0;
-                const ff ab = G == 32 ? energy_call<REL, 16, G>(A, t, cs, s0, ns, spc, mode, Ds, u, done)
-                                      : energy_call<REL, 32, G>(A, t, cs, s0, ns, spc, mode, Ds, u, done);
+                const ff ab = energy_call<REL, G>(A, t, cs, s0, ns, spc, mode, Ds, G == 32 ? 16 : 32, u, done);
                 if (side) {
                     Eaft1 = ff_sub(Eaft1, ab);
                     used1 = u;
@@ -1347,13 +1352,13 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
             if (!fail && !ff_is0(D0)) {
                 bool done;
                 const int mode = A.sort_by_weight ? sh.wmode[ic.a] : 1;
-                Eaft0 = ff_sub(Eaft0, energy_call<REL, 32, G>(A, t, cs, a0, na, ic.a, mode, D0, used0, done));
+                Eaft0 = ff_sub(Eaft0, energy_call<REL, G>(A, t, cs, a0, na, ic.a, mode, D0, 32, used0, done));
                 if (!done) fail0 = 1;
             }
             if (!fail && !fail0 && !intra && !ff_is0(D1)) {
                 bool done;
                 const int mode = A.sort_by_weight ? sh.wmode[ic.b] : 1;
-                Eaft1 = ff_sub(Eaft1, energy_call<REL, 32, G>(A, t, cs, b0, nb, ic.b, mode, D1, used1, done));
+                Eaft1 = ff_sub(Eaft1, energy_call<REL, G>(A, t, cs, b0, nb, ic.b, mode, D1, 32, used1, done));
                 if (!done) fail1 = 1;
             }
         }
