@@ -40,6 +40,7 @@ namespace mcc {
 namespace grp {
 
 
+
 // Bounds-checked build (-DMCC_DEBUG_BOUNDS): every tile and global index of the group kernels is checked against
 // the bound of what it indexes; the first violation latches kErrBounds in the status word and records (source line,
 // index, bound, count) in rec[0..3]; the access then uses index 0 instead (results are garbage, memory is safe).
@@ -1214,6 +1215,7 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
         for (int q = 0; q < 8; ++q) acc[q] = zero;
         for (int side = 0; side < nside; ++side) {
             const int s0 = side ? b0 : a0, ns = side ? nb : na;
+#pragma unroll 1  // rolled: a smaller instruction footprint
             for (int q = threadIdx.x; q < ns; q += G) {
                 const int i = s0 + q;
                 const float2 ws = t.w[CHK(t.dbg, i, t.n)];
@@ -1226,15 +1228,8 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
                 }
             }
         }
-        if (intra) {
-            ff r4[4] = {acc[0], acc[1], acc[2], zero};
-            gallreduce<G, 4>(r4, sh.red);
-            acc[0] = r4[0];
-            acc[1] = r4[1];
-            acc[2] = r4[2];
-        } else {
-            gallreduce<G, 8>(acc, sh.red);
-        }
+        // one reduction for intra and inter (the species-b slots are zero for intra): one copy of its code
+        gallreduce<G, 8>(acc, sh.red);
         const ff inv = ffq_div(ffk(1.f), intra ? sh.W2m[ic.a] : ff_add(sh.W2m[ic.a], sh.W2m[ic.b]));
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1251,6 +1246,7 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
     ff e2[2] = {zero, zero};
     for (int side = 0; side < nside; ++side) {
         const int s0 = side ? b0 : a0, ns = side ? nb : na;
+#pragma unroll 1  // rolled: a smaller instruction footprint
         for (int q = threadIdx.x; q < ns; q += G) {
             const int i = s0 + q;
             const float2 ws = t.w[CHK(t.dbg, i, t.n)];
@@ -1272,19 +1268,8 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
     // species a did not fail, and a failed interaction is replayed without it, so only the pair count of species b
     // is dropped when species a fails.
     const bool both = !intra && A.fail_policy == 0;
-    if (!both) {
-        if (intra) {
-            ff r1[1] = {e2[0]};
-            greduce_warp0<G, 1>(r1, sh.red);
-            e2[0] = r1[0];
-        } else {
-            greduce_warp0<G, 2>(e2, sh.red);
-        }
-    } else if (G == 32) {
-        greduce_warp0<G, 2>(e2, sh.red);
-    } else {
-        gallreduce<G, 2>(e2, sh.red);
-    }
+    if (!both || G == 32) greduce_warp0<G, 2>(e2, sh.red);  // intra: e2[1] is zero
+    else gallreduce<G, 2>(e2, sh.red);
     PHASE_MARK(pc, 4);
     // unit 0 runs species a (and b when not both), unit 1 species b
     const int unit = both ? (G == 32 ? lane >> 4 : warp) : (warp == 0 ? 0 : 2);
@@ -1422,6 +1407,7 @@ __device__ __forceinline__ void gload(const StepArgs& A, const GTile& t, GShared
         ff acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = zero;
+#pragma unroll 1  // rolled: a smaller instruction footprint
         for (int q = threadIdx.x; q < ns; q += G) {
             const int i = s0 + q;
             const float2 ws = split_weight(A.w[cs + CHK(t.dbg, i, t.n)]);
@@ -1520,6 +1506,7 @@ __device__ void gcell(const StepArgs& A, int c, unsigned char* dyn, GShared<G>& 
     // write back: the float-float state rounded once to float
     const int cap = t.cap;
     float* gv[3] = {reinterpret_cast<float*>(A.vx), reinterpret_cast<float*>(A.vy), reinterpret_cast<float*>(A.vz)};
+#pragma unroll 1  // rolled: a smaller instruction footprint
     for (int i = threadIdx.x; i < n; i += G) {
 #pragma unroll
         for (int d = 0; d < 3; ++d)
