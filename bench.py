@@ -82,10 +82,12 @@ DOMINANT_KERNEL_SOURCES = ("mcc_group.cuh", "mcc_group_f32.cu", "mcc_device.cuh"
 def kernel_source_hash() -> str:
     """Hash of the sources the mixed-path group kernels are compiled from (the committed ncu record is valid only
     for the kernel source it was taken on)."""
+    from paper_2407_19151_gb300 import _build
     h = hashlib.sha256()
     for f in DOMINANT_KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2407_19151_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    h.update(" ".join(_build.UNIT_FLAGS.get("mcc_group_f32.cu", [])).encode())  # the unit's compile flags
     return h.hexdigest()[:16]
 
 

@@ -17,6 +17,10 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 EXTRA = os.environ.get("MCC_NVCC_FLAGS", "").split()
+# The mixed-precision group kernels take float division and square root from the hardware approximations (about
+# 2 ulp), like the explicit fast intrinsics of their pair kinematics; every other unit keeps IEEE float division.
+UNIT_FLAGS = {"mcc_group_f32.cu": ["-prec-div=false", "-prec-sqrt=false"],
+              "mcc_group_f32rel.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def lib_path(debug_bounds: bool = False, phase_clocks: bool = False) -> str:
@@ -31,11 +35,13 @@ def source_hash() -> str:
     for f in [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "mcc.h")]:
         with open(f, "rb") as fh:
             h.update(fh.read())
+    h.update(repr(sorted(UNIT_FLAGS.items())).encode())
     return h.hexdigest()[:16]
 
 
 def _newest_input() -> float:
-    files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "mcc.h")]
+    files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "mcc.h"),
+                                                                 os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 
 
@@ -52,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None, de
 
     def compile_one(src: str) -> str:
         obj = os.path.join(os.path.dirname(out), f"{os.path.splitext(src)[0]}.{os.path.basename(out)}.o")
-        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *UNIT_FLAGS.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
