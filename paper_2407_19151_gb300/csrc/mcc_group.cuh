@@ -392,27 +392,31 @@ __device__ void gpermutations(const StepArgs& A, const GTile& t, GShared<G>& sh,
     const int L = B0 + B1;  // <= na + nb <= cap
     for (int b = threadIdx.x; b < L; b += G) cnt[CHK(t.dbg, b, t.cap)] = 0;
     gsync<G>();
-    for (int side = 0; side < nside; ++side) {
-        const int s0 = side ? b0 : a0, n = side ? nb : na, base = side ? B0 : 0, l = side ? lg1 : lg0;
-        const uint32_t tag = side ? kTagPermB : kTagPermA;
-        // two Philox blocks per thread and iteration: independent chains for the issue slots
-        for (int h = threadIdx.x; 2 * h < n; h += 2 * G) {
-            const int h2 = h + G;
-            const uint4 r = draw_at(A.rng, step, (uint32_t)h, (uint32_t)c, ictr, tag);
-            const uint4 r2 = draw_at(A.rng, step, (uint32_t)h2, (uint32_t)c, ictr, tag);
-            key[CHK(t.dbg, s0 + 2 * h, t.n)] = r.x;
+    // keys of both sides as one range of half-indices h (one Philox block per two particle indices of a side); two
+    // blocks per thread and iteration: independent chains for the issue slots
+    const int ha = (na + 1) / 2, htot = ha + (nside > 1 ? (nb + 1) / 2 : 0);
+    for (int h = threadIdx.x; h < htot; h += 2 * G) {
+        const int h2 = h + G;
+        const bool sb = h >= ha, sb2 = h2 >= ha;
+        const int hl = sb ? h - ha : h, hl2 = sb2 ? h2 - ha : h2;
+        const uint4 r = draw_at(A.rng, step, (uint32_t)hl, (uint32_t)c, ictr, sb ? kTagPermB : kTagPermA);
+        const uint4 r2 = draw_at(A.rng, step, (uint32_t)hl2, (uint32_t)c, ictr, sb2 ? kTagPermB : kTagPermA);
+        {
+            const int s0 = sb ? b0 : a0, n = sb ? nb : na, base = sb ? B0 : 0, l = sb ? lg1 : lg0;
+            key[CHK(t.dbg, s0 + 2 * hl, t.n)] = r.x;
             atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r.x >> (32 - l)) : 0), t.cap)], 1u);
-            if (2 * h + 1 < n) {
-                key[CHK(t.dbg, s0 + 2 * h + 1, t.n)] = r.z;
+            if (2 * hl + 1 < n) {
+                key[CHK(t.dbg, s0 + 2 * hl + 1, t.n)] = r.z;
                 atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r.z >> (32 - l)) : 0), t.cap)], 1u);
             }
-            if (2 * h2 < n) {
-                key[CHK(t.dbg, s0 + 2 * h2, t.n)] = r2.x;
-                atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r2.x >> (32 - l)) : 0), t.cap)], 1u);
-                if (2 * h2 + 1 < n) {
-                    key[CHK(t.dbg, s0 + 2 * h2 + 1, t.n)] = r2.z;
-                    atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r2.z >> (32 - l)) : 0), t.cap)], 1u);
-                }
+        }
+        if (h2 < htot) {
+            const int s0 = sb2 ? b0 : a0, n = sb2 ? nb : na, base = sb2 ? B0 : 0, l = sb2 ? lg1 : lg0;
+            key[CHK(t.dbg, s0 + 2 * hl2, t.n)] = r2.x;
+            atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r2.x >> (32 - l)) : 0), t.cap)], 1u);
+            if (2 * hl2 + 1 < n) {
+                key[CHK(t.dbg, s0 + 2 * hl2 + 1, t.n)] = r2.z;
+                atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(r2.z >> (32 - l)) : 0), t.cap)], 1u);
             }
         }
     }
@@ -432,10 +436,12 @@ __device__ void gpermutations(const StepArgs& A, const GTile& t, GShared<G>& sh,
         }
     }
     gsync<G>();
-    for (int side = 0; side < nside; ++side) {
-        const int s0 = side ? b0 : a0, n = side ? nb : na, base = side ? B0 : 0, l = side ? lg1 : lg0;
-        const int off = side ? na : 0;
-        for (int q = threadIdx.x; q < n; q += G) {
+    {
+        const int ntot = na + (nside > 1 ? nb : 0);  // both sides as one index range
+        for (int qq = threadIdx.x; qq < ntot; qq += G) {
+            const bool sb = qq >= na;
+            const int q = sb ? qq - na : qq;
+            const int s0 = sb ? b0 : a0, base = sb ? B0 : 0, l = sb ? lg1 : lg0, off = sb ? na : 0;
             const uint32_t k = key[CHK(t.dbg, s0 + q, t.n)];
             const int pos = (int)atomicAdd(&cnt[CHK(t.dbg, base + (l ? (int)(k >> (32 - l)) : 0), t.cap)], 1u) - off;
             t.perm[CHK(t.dbg, s0 + pos, t.n)] = (uint16_t)(s0 + q);
@@ -443,26 +449,26 @@ __device__ void gpermutations(const StepArgs& A, const GTile& t, GShared<G>& sh,
     }
     gsync<G>();
     // cnt[b] is now the end of bucket b: order each bucket by the full key (insertion sort)
-    for (int side = 0; side < nside; ++side) {
-        const int s0 = side ? b0 : a0, base = side ? B0 : 0, nbk = side ? B1 : B0, off = side ? na : 0;
-        const uint32_t tag = side ? kTagPermB : kTagPermA;
-        for (int b = threadIdx.x; b < nbk; b += G) {
-            const int end = (int)cnt[CHK(t.dbg, base + b, t.cap)] - off;
-            const int start = b ? (int)cnt[CHK(t.dbg, base + b - 1, t.cap)] - off : 0;
-            for (int x = start + 1; x < end; ++x) {
-                const int v = t.perm[CHK(t.dbg, s0 + x, t.n)];
-                const uint32_t kv = key[CHK(t.dbg, v, t.n)];
-                int y = x - 1;
-                while (y >= start) {
-                    const int u = t.perm[CHK(t.dbg, s0 + y, t.n)];
-                    const uint32_t ku = key[CHK(t.dbg, u, t.n)];
-                    const bool after = ku > kv || (ku == kv && key_lo_less(A, step, c, ictr, tag, v - s0, u - s0));
-                    if (!after) break;
-                    t.perm[CHK(t.dbg, s0 + y + 1, t.n)] = (uint16_t)u;
-                    --y;
-                }
-                t.perm[CHK(t.dbg, s0 + y + 1, t.n)] = (uint16_t)v;
+    for (int bb = threadIdx.x; bb < L; bb += G) {  // both sides' buckets as one range
+        const bool sb = bb >= B0;
+        const int b = sb ? bb - B0 : bb;
+        const int s0 = sb ? b0 : a0, base = sb ? B0 : 0, off = sb ? na : 0;
+        const uint32_t tag = sb ? kTagPermB : kTagPermA;
+        const int end = (int)cnt[CHK(t.dbg, base + b, t.cap)] - off;
+        const int start = b ? (int)cnt[CHK(t.dbg, base + b - 1, t.cap)] - off : 0;
+        for (int x = start + 1; x < end; ++x) {
+            const int v = t.perm[CHK(t.dbg, s0 + x, t.n)];
+            const uint32_t kv = key[CHK(t.dbg, v, t.n)];
+            int y = x - 1;
+            while (y >= start) {
+                const int u = t.perm[CHK(t.dbg, s0 + y, t.n)];
+                const uint32_t ku = key[CHK(t.dbg, u, t.n)];
+                const bool after = ku > kv || (ku == kv && key_lo_less(A, step, c, ictr, tag, v - s0, u - s0));
+                if (!after) break;
+                t.perm[CHK(t.dbg, s0 + y + 1, t.n)] = (uint16_t)u;
+                --y;
             }
+            t.perm[CHK(t.dbg, s0 + y + 1, t.n)] = (uint16_t)v;
         }
     }
     gsync<G>();
@@ -1213,19 +1219,19 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
         ff acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = zero;
-        for (int side = 0; side < nside; ++side) {
-            const int s0 = side ? b0 : a0, ns = side ? nb : na;
+        // both species' particles as one index range (fewer partly filled passes over the group)
+        const int ntot = na + (nside > 1 ? nb : 0);
 #pragma unroll 1  // rolled: a smaller instruction footprint
-            for (int q = threadIdx.x; q < ns; q += G) {
-                const int i = s0 + q;
-                const float2 ws = t.w[CHK(t.dbg, i, t.n)];
-                const ff w = {ws.x, ws.y};
+        for (int q = threadIdx.x; q < ntot; q += G) {
+            const bool sb = q >= na;
+            const int i = sb ? b0 + (q - na) : a0 + q;
+            const float2 ws = t.w[CHK(t.dbg, i, t.n)];
+            const ff w = {ws.x, ws.y};
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const ff x = ff_mul(w, ff_ld(t.v[d * cap + CHK(t.dbg, i, t.n)]));
-                    if (side) acc[3 + d] = ff_add(acc[3 + d], x);
-                    else acc[d] = ff_add(acc[d], x);
-                }
+            for (int d = 0; d < 3; ++d) {
+                const ff x = ff_mul(w, ff_ld(t.v[d * cap + CHK(t.dbg, i, t.n)]));
+                if (sb) acc[3 + d] = ff_add(acc[3 + d], x);
+                else acc[d] = ff_add(acc[d], x);
             }
         }
         // one reduction for intra and inter (the species-b slots are zero for intra): one copy of its code
@@ -1244,11 +1250,12 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
     PHASE_MARK(pc, 3);
     // momentum shift v_pm = v_ps - B w_p (Eq. vp_pm) and the post-shift species energies (Eq. DeltaEs)
     ff e2[2] = {zero, zero};
-    for (int side = 0; side < nside; ++side) {
-        const int s0 = side ? b0 : a0, ns = side ? nb : na;
+    {
+        const int ntot = na + (nside > 1 ? nb : 0);
 #pragma unroll 1  // rolled: a smaller instruction footprint
-        for (int q = threadIdx.x; q < ns; q += G) {
-            const int i = s0 + q;
+        for (int q = threadIdx.x; q < ntot; q += G) {
+            const bool sb = q >= na;
+            const int i = sb ? b0 + (q - na) : a0 + q;
             const float2 ws = t.w[CHK(t.dbg, i, t.n)];
             const ff w = {ws.x, ws.y};
             ff v[3];
@@ -1258,7 +1265,7 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
                 t.v[d * cap + CHK(t.dbg, i, t.n)] = ff_st(v[d]);
             }
             const ff kp = ff_mul(w, ke_per_mass<REL>(v, c2inv));
-            if (side) e2[1] = ff_add(e2[1], kp);
+            if (sb) e2[1] = ff_add(e2[1], kp);
             else e2[0] = ff_add(e2[0], kp);
         }
     }
