@@ -1378,9 +1378,11 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
         }
     }
     gsync<G>();
+    // every thread reads the outcome; thread 0 updates the carried sums, which are read again only after the next
+    // interaction's barriers (so no barrier closes this one)
+    const int fa = sh.eres_i[1], fb = sh.eres_i[3];
+    const int fail = fa | fb;
     if (threadIdx.x == 0) {
-        const int fa = sh.eres_i[1], fb = sh.eres_i[3];
-        const int fail = fa | fb;
         sh.used_k[k] = sh.eres_i[0] + (fa ? 0 : sh.eres_i[2]);
         sh.fail_k[k] = fail;
         sh.E[ic.a] = sh.eres_E[0];
@@ -1393,9 +1395,8 @@ __device__ int gcorrect(const StepArgs& A, const GTile& t, GShared<G>& sh, int c
         }
         if (fail && A.fail_policy == 2) latch(A.status, kErrCorrectionFailed);
     }
-    gsync<G>();
     PHASE_MARK(pc, 5);
-    return (sh.fail_k[k] && A.fail_policy == 0) ? 1 : 0;
+    return (fail && A.fail_policy == 0) ? 1 : 0;
 }
 
 // ----------------------------------------------------------------------------------------------- cell visit
