@@ -487,25 +487,20 @@ __device__ __forceinline__ void sort_keys(uint64_t* key, int n)
 }
 
 // Weight-descending order of each species, once per visit (optional step of Algorithm 1): a segment stored with
-// strictly increasing keys needs no order (mode 3); distinct keys fix the order for the visit (mode 0); all equal
+// strictly increasing keys needs no order (mode 3; the cell load finds these and passes the others in `need`);
+// distinct keys fix the order for the visit (mode 0); all equal
 // make it the random permutation (mode 1); partial ties sort it per interaction (mode 2). The species that need a
 // sort are sorted at once, species s by warp s mod (G / 32) (segments above the one-warp sort by the whole group,
 // one after another).
 template <int G>
-__device__ __noinline__ void gweight_order(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t cs, int S)
+__device__ __noinline__ void gweight_order(const StepArgs& A, const GTile& t, GShared<G>& sh, int64_t cs, int S,
+                                           unsigned need)
 {
     constexpr int kWarps = G / 32;
     const int warp = threadIdx.x >> 5;
-    unsigned need = 0;  // species whose segment is not stored in strictly descending weight
-    for (int sp = 0; sp < S; ++sp) {
-        const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
-        bool bad = false;
-        for (int q = threadIdx.x; q + 1 < ns; q += G)
-            bad |= weight_key(A.w[cs + CHK(t.dbg, s0 + q, t.n)], 0) >=
-                   weight_key(A.w[cs + CHK(t.dbg, s0 + q + 1, t.n)], 0);
-        if (gany<G>(bad)) need |= 1u << sp;
-        else if (threadIdx.x == 0) sh.wmode[sp] = 3;
-    }
+    if (threadIdx.x == 0)
+        for (int sp = 0; sp < S; ++sp)
+            if (!(need >> sp & 1u)) sh.wmode[sp] = 3;
     if (!need) return;
     for (int sp = 0; sp < S; ++sp) {
         if (!(need >> sp & 1u)) continue;
@@ -1410,15 +1405,21 @@ __device__ __forceinline__ void gload(const StepArgs& A, const GTile& t, GShared
     const ff zero = {0.f, 0.f};
     const ff c2inv = {A.c2inv_f, A.c2inv_lo};
     ff tot[4] = {zero, zero, zero, zero};
+    const bool order = A.correct && A.sort_by_weight;
+    unsigned need = 0;  // species whose segment is not stored in strictly descending weight
     for (int sp = 0; sp < S; ++sp) {
         const int s0 = sh.off[sp], ns = sh.off[sp + 1] - s0;
         ff acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = zero;
+        float unordered = 0.f;  // neighbours out of the stored weight order (counted in slot 6 of the reduction)
 #pragma unroll 1  // rolled: a smaller instruction footprint
         for (int q = threadIdx.x; q < ns; q += G) {
             const int i = s0 + q;
-            const float2 ws = split_weight(A.w[cs + CHK(t.dbg, i, t.n)]);
+            const double wd = A.w[cs + CHK(t.dbg, i, t.n)];
+            if (order && q + 1 < ns && weight_key(wd, 0) >= weight_key(A.w[cs + CHK(t.dbg, i + 1, t.n)], 0))
+                unordered += 1.f;
+            const float2 ws = split_weight(wd);
             t.w[CHK(t.dbg, i, t.n)] = ws;
             const ff w = {ws.x, ws.y};
             ff v[3];
@@ -1432,7 +1433,9 @@ __device__ __forceinline__ void gload(const StepArgs& A, const GTile& t, GShared
             acc[1] = ff_add(acc[1], ff_mul(w, w));
             acc[5] = ff_add(acc[5], ff_mul(w, ke_per_mass<REL>(v, c2inv)));
         }
+        acc[6] = ffk(unordered);
         gallreduce<G, 8>(acc, sh.red);
+        if (acc[6].hi > 0.f) need |= 1u << sp;
         const ff m = mass_ff(A, sp);
         const ff Pm[3] = {ff_mul(m, acc[2]), ff_mul(m, acc[3]), ff_mul(m, acc[4])};
         const ff Em = ff_mul(m, acc[5]);
@@ -1456,7 +1459,7 @@ __device__ __forceinline__ void gload(const StepArgs& A, const GTile& t, GShared
         sh.E0 = tot[3];
     }
     gsync<G>();
-    if (A.correct && A.sort_by_weight) gweight_order<G>(A, t, sh, cs, S);
+    if (order) gweight_order<G>(A, t, sh, cs, S, need);
 }
 
 template <bool REL, int G>
