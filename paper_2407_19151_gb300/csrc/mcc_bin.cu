@@ -193,14 +193,17 @@ __device__ __forceinline__ void warp_sort_smem(int n, Cmpx cmpx)
 // straight into the weight order of mcc_bin_weighted: pairs (weight key with a zero rank field, particle index)
 // sorted lexicographically, which is descending truncated weight with ties in increasing index. The ids of the
 // larger segments are appended to `large` (large[0] the count, zeroed before) for the CTA-wide sorts.
+// WEIGHTED: the weight-order keys need a second slab; the index-only sort keeps 2 KB per warp, so that more warps
+// fit an SM (the sorts are latency-bound).
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __restrict__ offsets, int64_t nk,
                                                               const double* __restrict__ w, int32_t* __restrict__ perm,
                                                               int32_t* __restrict__ large)
 {
-    __shared__ uint64_t kslab[kBinThreads / 32][kWarpSeg];
+    __shared__ uint64_t kslab[WEIGHTED ? kBinThreads / 32 : 1][WEIGHTED ? kWarpSeg : 1];
     __shared__ int32_t islab[kBinThreads / 32][kWarpSeg];
     const int lane = threadIdx.x & 31;
-    uint64_t* kb = kslab[threadIdx.x >> 5];
+    uint64_t* kb = kslab[WEIGHTED ? threadIdx.x >> 5 : 0];
     int32_t* ib = islab[threadIdx.x >> 5];
     const int64_t warp = ((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kBinThreads) >> 5;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(kBinThreads) k_segsort_warp(const int64_t* __r
         if (n > kWarpSeg && lane == 0) large[1 + atomicAdd(&large[0], 1)] = (int32_t)seg;
         if (n < 2 || n > kWarpSeg) continue;
         int32_t* p = perm + b;
-        if (w == nullptr) {
+        if (!WEIGHTED) {
             for (int i = lane; i < n; i += 32) ib[i] = p[i];
             __syncwarp();
             warp_sort_smem(n, [ib](int lo, int hi) {
@@ -348,7 +351,10 @@ static cudaError_t bin_core(const int32_t* cell, const int32_t* species, int64_t
     *launches += 3;
     if (n > 0) {
         k_scatter<<<g, kBinThreads, 0, st>>>(cell, species, n, n_cells, n_species, offsets, cursor, perm);
-        k_segsort_warp<<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm, large);
+        if (w)
+            k_segsort_warp<true><<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm, large);
+        else
+            k_segsort_warp<false><<<grid_for(nk * 32, kBinThreads), kBinThreads, 0, st>>>(offsets, nk, w, perm, large);
         k_segsort<<<grid_for(n / (kWarpSeg + 1) * kBinThreads, kBinThreads), kBinThreads, 0, st>>>(offsets, large,
                                                                                                  perm);
         *launches += 4;
