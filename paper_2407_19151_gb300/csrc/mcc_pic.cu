@@ -81,17 +81,35 @@ struct GatherN {
     int32_t n_arrays;
 };
 
+// Four elements per thread and iteration (their permutation entries loaded first, then every array's four reads
+// issued together): more reads in flight per thread for the latency of the permuted loads.
+constexpr int kGatherUnroll = 4;
+
+template <class T>
+__device__ __forceinline__ void gather4(const void* in, void* out, const int64_t (&p)[kGatherUnroll], int64_t base,
+                                        int64_t stride, int64_t n)
+{
+    T v[kGatherUnroll];
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u)
+        v[u] = base + u * stride < n ? __ldg(static_cast<const T*>(in) + p[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u)
+        if (base + u * stride < n) static_cast<T*>(out)[base + u * stride] = v[u];
+}
+
 __global__ void __launch_bounds__(kPushThreads) k_gather_n(GatherN a, const int32_t* __restrict__ perm, int64_t n)
 {
-    for (int64_t k = (int64_t)blockIdx.x * kPushThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kPushThreads) {
-        const int64_t p = perm[k];
+    const int64_t stride = (int64_t)gridDim.x * kPushThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kPushThreads + threadIdx.x; base < n; base += kGatherUnroll * stride) {
+        int64_t p[kGatherUnroll];
+#pragma unroll
+        for (int u = 0; u < kGatherUnroll; ++u) p[u] = base + u * stride < n ? perm[base + u * stride] : 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (j >= a.n_arrays) break;
-            if (a.bytes[j] == 8)
-                static_cast<uint64_t*>(a.out[j])[k] = __ldg(static_cast<const uint64_t*>(a.in[j]) + p);
-            else
-                static_cast<uint32_t*>(a.out[j])[k] = __ldg(static_cast<const uint32_t*>(a.in[j]) + p);
+            if (a.bytes[j] == 8) gather4<uint64_t>(a.in[j], a.out[j], p, base, stride, n);
+            else gather4<uint32_t>(a.in[j], a.out[j], p, base, stride, n);
         }
     }
 }
