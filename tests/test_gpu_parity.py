@@ -270,6 +270,40 @@ def test_fused_mixed_precision(mcc, name, make):
     assert err.max() < 1e-5, err.max()
 
 
+def test_fused_mixed_precision_full_size_sampled(mcc):
+    """The benchmark's workload at full size (three species, 2^18 cells, 1.34e8 particles, segments in weight order)
+    in the launch configuration the benchmark times (mixed path, automatic class capacities, every size class, one
+    fused step), checked on sampled cells against the oracle stepped on those cells alone (every draw is keyed by
+    the global cell id, so a cell's step does not depend on the others): the first 512 cells, the largest cell, and
+    256 cells drawn at random. The bounds of test_fused_mixed_precision: the same failed corrections, 99.9% of the
+    sampled particles within 2e-6 and every one within 1e-5."""
+    wl = W.three_species(n_cells=1 << 18).weight_ordered()
+    C, S = wl.n_cells, wl.n_species
+    tot = wl.counts.sum(axis=1)
+    v, w, off = device_state(wl, "f32")
+    pp, op = _params(mcc, wl)
+    _, fail = mcc.mcc_step_fused(*v, w, off, C, S, _species(wl), wl.lnL, pp, n_steps=1, max_cell=int(tot.max()))
+    mcc.sync_status(0)
+    got = gpu_velocities(v)
+    fail = fail.cpu().numpy()
+    del v, w, off
+    rng = np.random.default_rng(20240719)
+    cells = np.unique(np.concatenate([np.arange(512), [int(np.argmax(tot))], rng.choice(C, 256, replace=False)]))
+    st = oracle_state(wl, "f32")
+    rf = np.zeros(C, dtype=np.int32)
+    for c in cells:  # one oracle call per sampled cell (its global id, its own draws)
+        _, f = O.step(st, wl.q, wl.m, wl.lnL, op, n_steps=1, cell_begin=int(c), cell_end=int(c) + 1)
+        rf[c] = f[c]
+    np.testing.assert_array_equal(fail[cells], rf[cells])
+    # the sampled cells' particles, in cell order, with their (cell, species) segment offsets among them
+    sel = np.flatnonzero(np.isin(np.repeat(np.arange(C), tot), cells))
+    seg = np.concatenate([[0], np.cumsum(wl.counts[cells].reshape(-1))])
+    ref = np.stack([st.vx[sel], st.vy[sel], st.vz[sel]], axis=1)
+    err = velocity_error(got[sel], ref, seg)
+    assert np.quantile(err, 0.999) < F32_TOL, np.quantile(err, 0.999)
+    assert err.max() < 1e-5, err.max()
+
+
 @pytest.mark.parametrize("data_seed", [1239, 1241])
 def test_fused_mixed_precision_tiny_cells(mcc, data_seed):
     """Mixed path on cells of 1 to ~24 particles (species of 0-5: inactive and one-pair interactions, odd triplets,
