@@ -270,14 +270,20 @@ def test_fused_mixed_precision(mcc, name, make):
     assert err.max() < 1e-5, err.max()
 
 
-def test_fused_mixed_precision_full_size_sampled(mcc):
-    """The benchmark's workload at full size (three species, 2^18 cells, 1.34e8 particles, segments in weight order)
-    in the launch configuration the benchmark times (mixed path, automatic class capacities, every size class, one
-    fused step), checked on sampled cells against the oracle stepped on those cells alone (every draw is keyed by
+@pytest.mark.parametrize("name,make", [
+    ("three_species", lambda: W.three_species(n_cells=1 << 18).weight_ordered()),
+    ("equilibration_ta77", lambda: W.equilibration(precision="f32", method=W.TA77)),
+    ("relativistic_beam", lambda: W.relativistic_beam()),
+], ids=["three_species", "equilibration_ta77", "relativistic_beam"])
+def test_fused_mixed_precision_full_size_sampled(mcc, name, make):
+    """The mixed-precision workloads at their full sizes (three species: 2^18 cells, 1.34e8 particles, segments in
+    weight order, the benchmark's workload; two-species equilibration: 4096 cells; relativistic beam: 65536 cells,
+    1.16e7 particles) in the launch configuration the benchmark times (automatic class capacities, every size class,
+    one fused step), checked on sampled cells against the oracle stepped on those cells alone (every draw is keyed by
     the global cell id, so a cell's step does not depend on the others): the first 512 cells, the largest cell, and
     256 cells drawn at random. The bounds of test_fused_mixed_precision: the same failed corrections, 99.9% of the
     sampled particles within 2e-6 and every one within 1e-5."""
-    wl = W.three_species(n_cells=1 << 18).weight_ordered()
+    wl = make()
     C, S = wl.n_cells, wl.n_species
     tot = wl.counts.sum(axis=1)
     v, w, off = device_state(wl, "f32")
@@ -288,7 +294,8 @@ def test_fused_mixed_precision_full_size_sampled(mcc):
     fail = fail.cpu().numpy()
     del v, w, off
     rng = np.random.default_rng(20240719)
-    cells = np.unique(np.concatenate([np.arange(512), [int(np.argmax(tot))], rng.choice(C, 256, replace=False)]))
+    cells = np.unique(np.concatenate([np.arange(min(512, C)), [int(np.argmax(tot))],
+                                      rng.choice(C, 256, replace=False)]))
     st = oracle_state(wl, "f32")
     rf = np.zeros(C, dtype=np.int32)
     for c in cells:  # one oracle call per sampled cell (its global id, its own draws)
