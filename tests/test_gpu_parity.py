@@ -186,6 +186,10 @@ FUSED_F64 = [
     ("duplicity_ta77", lambda: W.equilibration(n_cells=48, mean_count=40, precision="f64", method=W.TA77),
      {"weighting": 1, "dt_scale": 5}),
     ("ordered_key_ties", lambda: _key_ties(W.three_species(n_cells=40, mean_count=200, precision="f64")), {}),
+    # full sizes: the isotropisation workload (64 cells x 128) and the differentiable workload's forward step
+    # (1024 cells x 512, two species)
+    ("isotropisation_full_size", lambda: W.isotropisation(), {}),
+    ("differentiable_full_size", lambda: W.differentiable(), {}),
 ]
 
 
