@@ -112,6 +112,39 @@ def test_adjoint_conservation_closed_forms(mcc, method, case):
     assert np.abs(gL).max() < 1e-9 * (mw * ef).sum()
 
 
+@pytest.mark.parametrize("tape", [False, True], ids=["checkpoints", "tape"])
+def test_adjoint_conservation_closed_forms_full_size(mcc, tape):
+    """The differentiable workload at full size (1024 cells x 512, two species, N97, FP64) over its 50 steps with a
+    checkpoint every 10 (or recorded tapes), as the benchmark runs it: the momentum and energy closed forms of
+    test_adjoint_conservation_closed_forms hold for every particle, since every step conserves both exactly."""
+    wl = W.differentiable()
+    kw = dict(method=wl.method, dt=wl.dt, fE=wl.fE, seed=wl.seed, step=0)
+    sp = wl.species_of_particles()
+    mw = wl.m[sp] * wl.w
+    v0 = np.stack([wl.vx, wl.vy, wl.vz], axis=1)
+
+    def cot_p(vf):
+        c = np.zeros_like(vf)
+        c[:, 0] = mw
+        return c
+
+    vf, gv, gw, gL = _grads(mcc, wl, kw, cot_p, n_steps=50, every=10, tape=tape)
+    scale = mw * np.maximum(np.abs(v0).max(1), np.abs(vf).max(1))
+    want = np.zeros_like(v0)
+    want[:, 0] = mw
+    assert (np.abs(gv - want).max(1) / mw).max() < 1e-9
+    assert (np.abs(gw - wl.m[sp] * (v0[:, 0] - vf[:, 0])) * wl.w / scale).max() < 1e-9
+    assert np.abs(gL).max() < 1e-9 * np.abs(mw[:, None] * vf).sum()
+
+    vf, gv, gw, gL = _grads(mcc, wl, kw, lambda vf: mw[:, None] * vf, n_steps=50, every=10, tape=tape)
+    e0 = (v0 ** 2).sum(1)
+    ef = (vf ** 2).sum(1)
+    escale = mw * np.maximum(e0, ef)
+    assert (np.abs(gv - mw[:, None] * v0).max(1) * np.abs(v0).max(1) / escale).max() < 1e-9
+    assert (np.abs(gw - 0.5 * wl.m[sp] * (e0 - ef)) * wl.w / escale).max() < 1e-9
+    assert np.abs(gL).max() < 1e-9 * (mw * ef).sum()
+
+
 @pytest.mark.parametrize("case", ["even", "poisson"])
 @pytest.mark.parametrize("method", [W.TA77, W.N97])
 def test_adjoint_matches_oracle_finite_differences(mcc, method, case):
