@@ -36,9 +36,10 @@ def _params(mcc, wl, **kw):
 
 # ------------------------------------------------------------------------------------------------- binning
 # segment sizes: ~50, ~24 and ~6 (one warp per segment; the last over 13 scan tiles), ~625 (one CTA, shared memory),
-# ~30000 (one CTA, in place)
+# ~30000 (one CTA, in place); ~171 at full size
 BIN_CASES = [(0, 4, 2), (1, 1, 1), (1000, 7, 3), (200_000, 4096, 2), (300_000, 25_000, 2), (20_000, 16, 2),
-             (30_000, 3, 1)]
+             (30_000, 3, 1),
+             (134_296_981, 1 << 18, 3)]  # the benchmark's full size: 1.34e8 particles in 2^18 cells x 3 species
 
 
 @pytest.mark.parametrize("n,C,S", BIN_CASES)
