@@ -295,6 +295,8 @@ int mcc_push(const mcc_particles* P, void* x, void* y, void* z, const mcc_grid* 
  * Output slots: cell c's pairs start at offsets[c * n_species] (its first particle); a cell never has more pairs
  * than particles, so pair_i / pair_j / pair_flags of length n suffice. Entries beyond a cell's pair count are not
  * written. pair_i holds species-sa particles, pair_j species-sb particles, both as global binned indices.
+ * A cell is paired in one CTA's shared memory (20 B per particle: about 11,000 particles on GB300); a larger cell
+ * is skipped and latches the bounds error (MCC_ERR_BOUNDS from mcc_sync_status).
  */
 int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_species, int32_t sa, int32_t sb,
              int32_t inter, uint64_t seed, uint64_t step, int32_t* pair_i, int32_t* pair_j, uint8_t* pair_flags,

@@ -240,6 +240,14 @@ size_t max_tile_particles(const mcc_ctx* ctx, bool f32)
     return avail / mcc::tile_bytes_per_particle(f32);
 }
 
+// Largest cell of the pairing mode (its compact tile in one CTA's shared memory).
+size_t max_pair_tile_particles(const mcc_ctx* ctx)
+{
+    const size_t fixed = mcc::cell_kernel_static_smem(false, false, mcc::kPair) + kStaticSmemReserve;
+    const size_t avail = ctx->smem_optin > fixed ? ctx->smem_optin - fixed : 0;
+    return avail / mcc::pair_tile_bytes_per_particle();
+}
+
 // Automatic tile: the largest that still lets kAutoCtasPerSm CTAs share an SM's shared memory.
 int auto_tile(const mcc_ctx* ctx, bool f32)
 {
@@ -254,7 +262,8 @@ int auto_tile(const mcc_ctx* ctx, bool f32)
 int run_cells(mcc_ctx* ctx, StepArgs& a, bool f32, bool rel, int mode, int cap, cudaStream_t st,
               int max_grid = 1 << 30)
 {
-    const size_t smem = (size_t)cap * mcc::tile_bytes_per_particle(f32);
+    const size_t per = mode == mcc::kPair ? mcc::pair_tile_bytes_per_particle() : mcc::tile_bytes_per_particle(f32);
+    const size_t smem = (size_t)cap * per;
     if (mcc::set_cell_smem_limit(f32, rel, mode, smem) != cudaSuccess) return MCC_ERR_CUDA;
     int bps = mcc::cell_kernel_blocks_per_sm(f32, rel, mode, smem);
     if (bps < 1) return MCC_ERR_CUDA;
@@ -481,7 +490,7 @@ int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_sp
     a.pair_i = pair_i;
     a.pair_j = pair_j;
     a.pair_flags = pair_flags;
-    const int cap = (int)max_tile_particles(ctx, false);
+    const int cap = (int)max_pair_tile_particles(ctx);
     return run_cells(ctx, a, false, false, mcc::kPair, cap, S(stream));
 }
 

@@ -67,6 +67,25 @@ __device__ __forceinline__ Tile<V> make_tile(unsigned char* base, int cap)
     return t;
 }
 
+// Tile of the pairing mode: keys | permutation | bucket counters (2 per particle: both sides' next powers of two of
+// their counts add up to less than twice the cell's count); no velocities, weights or weight order.
+template <class V>
+__device__ __forceinline__ Tile<V> make_pair_tile(unsigned char* base, int cap)
+{
+    Tile<V> t;
+    t.cap = cap;
+    t.vs = t.bs = cap;
+    t.keys = reinterpret_cast<uint64_t*>(base);
+    t.w = nullptr;
+    t.v = nullptr;
+    t.vb = nullptr;
+    t.perm = reinterpret_cast<int32_t*>(base + 8 * (size_t)cap);
+    t.rho = t.perm;
+    t.cnt = reinterpret_cast<uint32_t*>(base + 12 * (size_t)cap);
+    t.cnt_cap = 2 * cap;
+    return t;
+}
+
 // A cell above the on-chip tile runs from its CTA's global slab; the shared-memory tile (smem bytes) is then idle,
 // so the arrays that fit move there, in order of how much they gain: the bucket counters (shared-memory atomics),
 // velocities and weights (random access by pair), sort keys, permutation, weight order, pre-interaction copy.
@@ -948,7 +967,13 @@ __device__ void process_cell(const StepArgs& A, int c, unsigned char* dyn, Share
     const int64_t cs = A.offsets[(int64_t)c * S];
     const int n = (int)(A.offsets[(int64_t)(c + 1) * S] - cs);
     Tile<V> t;
-    if (n <= A.cap) {
+    if (MODE == kPair) {
+        if (n > A.cap) {
+            if (threadIdx.x == 0) latch(A.status, kErrBounds);
+            return;
+        }
+        t = make_pair_tile<V>(dyn, A.cap);
+    } else if (n <= A.cap) {
         t = make_tile<V>(dyn, A.cap);
     } else if (A.slab != nullptr && n <= A.slab_cap) {
         t = make_tile<V>(reinterpret_cast<unsigned char*>(A.slab) + (size_t)blockIdx.x * (size_t)A.slab_stride,

@@ -132,6 +132,32 @@ def test_pair_bit_exact(mcc, name, counts):
             np.testing.assert_array_equal(fl[sl].cpu().numpy(), rf[sl])
 
 
+def test_pair_bit_exact_full_size(mcc):
+    """The benchmark's cell counts at full size (2^18 cells x 3 species, 1.34e8 particles): the random permutations
+    and the Takizuka-Abe pairs of an intra-species and two inter-species interactions, every pair slot of every cell
+    bit-exact against the oracle."""
+    import torch
+    counts = W.three_species_counts()
+    C_, S = counts.shape
+    off = np.concatenate([[0], np.cumsum(counts.reshape(-1))]).astype(np.int64)
+    toff = torch.from_numpy(off).cuda()
+    for k, (a, b) in enumerate([(0, 0), (0, 1), (1, 2)]):
+        pi, pj, fl = mcc.mcc_pair(toff, C_, S, a, b, k, 0xABCDEF0123, 11)
+        mcc.sync_status(0)
+        ri, rj, rf = O.pairs(off, C_, S, a, b, k, 0xABCDEF0123, 11)
+        na, nb = counts[:, a], counts[:, b]
+        if a == b:
+            npairs = np.where(na < 2, 0, np.where(na % 2 == 0, na // 2, (na + 3) // 2))
+        else:
+            npairs = np.where((na > 0) & (nb > 0), np.maximum(na, nb), 0)
+        # pair slot q of cell c sits at off[c S] + q
+        start = off[:-1:S]
+        slot = np.repeat(start, npairs) + (np.arange(npairs.sum()) - np.repeat(np.cumsum(npairs) - npairs, npairs))
+        np.testing.assert_array_equal(pi.cpu().numpy()[slot], ri[slot])
+        np.testing.assert_array_equal(pj.cpu().numpy()[slot], rj[slot])
+        np.testing.assert_array_equal(fl.cpu().numpy()[slot], rf[slot])
+
+
 # ------------------------------------------------------------------------------------------------- unfused calls
 @pytest.mark.parametrize("method", [W.TA77, W.N97])
 def test_scatter_then_correct_fp64(mcc, method):
