@@ -312,6 +312,9 @@ int mcc_pair(mcc_ctx* ctx, const int64_t* offsets, int32_t n_cells, int32_t n_sp
  *   pair_*: output of mcc_pair for the same (sa, sb, inter, seed, step)
  *   backup: device, 3 * n values of the particle precision ([x | y | z] planes, binned index): receives the
  *           pre-scatter velocities of every particle of species sa and sb (used by mcc_correct)
+ * mcc_scatter and mcc_correct hold a cell in one CTA's shared memory (72 B per particle in FP64, about 3,100
+ * particles on GB300; 48 B on the mixed path, about 4,700); a larger cell is skipped and latches MCC_ERR_BOUNDS.
+ * mcc_step_fused has no such limit (its workspace holds the cells above the on-chip tile).
  */
 int mcc_scatter(mcc_ctx* ctx, const mcc_particles* particles, const int64_t* offsets, int32_t n_cells,
                 int32_t n_species, const mcc_species* sp, const double* lnL, int32_t sa, int32_t sb, int32_t inter,

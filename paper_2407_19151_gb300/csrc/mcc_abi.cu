@@ -36,6 +36,9 @@ struct mcc_ctx {
 
 namespace mcc {
 
+// Bytes per particle of the pairing mode's tile (defined with its kernel, mcc_cell.cu).
+size_t pair_tile_bytes_per_particle();
+
 // N97 table on the host, in double: A(s) solves G(A) = 1 - coth A + 1/A = 1 - e^-s (bisection to the last bit);
 // stored as f = ln(A s) and h df/dx at x = ln s, where df/dx = 1 + s e^-s / (A G'(A)) by implicit
 // differentiation, G'(A) = -(1/A^2 - 1/sinh^2 A).
@@ -240,7 +243,8 @@ size_t max_tile_particles(const mcc_ctx* ctx, bool f32)
     return avail / mcc::tile_bytes_per_particle(f32);
 }
 
-// Largest cell of the pairing mode (its compact tile in one CTA's shared memory).
+// Largest cell of the pairing mode (its compact tile in one CTA's shared memory; the tile layout and its bytes per
+// particle are defined with the kernel, in mcc_cell.cu).
 size_t max_pair_tile_particles(const mcc_ctx* ctx)
 {
     const size_t fixed = mcc::cell_kernel_static_smem(false, false, mcc::kPair) + kStaticSmemReserve;

@@ -68,7 +68,10 @@ __device__ __forceinline__ Tile<V> make_tile(unsigned char* base, int cap)
 }
 
 // Tile of the pairing mode: keys | permutation | bucket counters (2 per particle: both sides' next powers of two of
-// their counts add up to less than twice the cell's count); no velocities, weights or weight order.
+// their counts add up to less than twice the cell's count); no velocities, weights or weight order. A tile of these
+// holds cells about three times larger than the step's tile.
+constexpr size_t kPairTileBytesPerParticle = 8 + 4 + 2 * 4;
+
 template <class V>
 __device__ __forceinline__ Tile<V> make_pair_tile(unsigned char* base, int cap)
 {
@@ -1250,6 +1253,8 @@ cudaError_t launch_group(bool f32, bool rel, int cls, const StepArgs& a, int gri
     void* args[] = {const_cast<StepArgs*>(&a)};
     return cudaLaunchKernel(group_kernel(f32, rel, cls), dim3(grid), dim3(32 << cls), args, smem, st);
 }
+
+size_t pair_tile_bytes_per_particle() { return kPairTileBytesPerParticle; }
 
 cudaError_t launch_cell(bool f32, bool rel, int mode, const StepArgs& a, int grid, size_t smem, cudaStream_t st)
 {

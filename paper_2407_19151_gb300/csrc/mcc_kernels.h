@@ -89,9 +89,6 @@ constexpr int kGroupWarpsPerSm = MCC_GROUP_WARPS_PER_SM;
 
 // Bytes per particle of the cell tile (keys, weights, velocities, pre-scatter copy, permutation, weight order).
 __host__ __device__ inline size_t tile_bytes_per_particle(bool f32) { return 8 + 8 + (f32 ? 6 * 4 : 6 * 8) + 4 + 4; }
-// The pairing mode (mcc_pair) holds only the sort keys, the permutation and the bucket counters (up to two per
-// particle): a tile of these holds cells about three times larger.
-__host__ __device__ inline size_t pair_tile_bytes_per_particle() { return 8 + 4 + 2 * 4; }
 
 // Shared-memory bytes per particle of the group kernels' cell tile (state, weight, scratch, two orders).
 constexpr size_t kGroupBytesPerParticle = 44;
